@@ -1,0 +1,355 @@
+"""Pins of the LOBPCG oracle against the paper's worked example, the algorithms'
+output contracts, closed-form spectra, brute force and invariances."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense
+from oracle import lobpcg as L
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            out[k] = [float(x) for x in v]
+    return out
+
+
+def _pencil(A, b=None, kdiag=None):
+    return L.Pencil(A.n, (A.rowptr, A.col, A.val), b, kdiag)
+
+
+def _run(p, seed=0, opts=None, scaleA=1.0, scaleB=None, nx=None):
+    A = synth.CSR(p.A.n, p.A.rowptr, p.A.col, p.A.val * scaleA)
+    b = p.b_diag
+    if scaleB is not None:
+        b = (np.ones(A.n) if b is None else b) * scaleB
+    kd = None if p.kdiag is None else p.kdiag * scaleA
+    pen = _pencil(A, b, kd)
+    nx = nx or synth.block_width(p.k, A.n)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, A.n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, 16, A.n)
+    return pen, L.lobpcg(pen, X0, p.k, p.tol, Om, opts)
+
+
+# ---------------------------------------------------------------- Sec. 4.1
+
+def _e1():
+    g = _golden("e1_worked_example.txt")
+    m = int(g["m"][0])
+    A = synth.tridiag(m, 3.0, 1.0)
+    X0 = np.zeros((m, 2))
+    X0[0] = [1, 1]
+    X0[1] = [-1, 1]
+    X0 /= np.sqrt(2)
+    return g, A, _pencil(A), X0
+
+
+def test_e1_theta0_and_w0():
+    g, A, pen, X0 = _e1()
+    AX = pen.A_mul(X0)
+    np.testing.assert_allclose(X0.T @ AX, np.diag(g["theta0"]), atol=1e-15)
+    C, theta = L.rayleigh_ritz(X0.T @ AX, X0.T @ X0)
+    np.testing.assert_allclose(theta, g["theta0"], atol=1e-14)
+    W0 = AX - X0 * np.array(g["theta0"])
+    expect = np.zeros_like(W0)
+    expect[int(g["w0_row"][0]) - 1] = g["w0_values"]
+    np.testing.assert_allclose(W0, expect, atol=1e-15)
+
+
+def test_e1_ortho_drop_keeps_one_column_and_ritz_values():
+    g, A, pen, X0 = _e1()
+    W0 = pen.A_mul(X0) - X0 * np.array(g["theta0"])
+    U, BU = L.ortho_drop(pen.B_mul, W0, X0, X0, 100 * L.EPS)
+    assert U.shape[1] == int(g["span_dim"][0]) - 2
+    e3 = np.zeros(A.n)
+    e3[2] = 1
+    np.testing.assert_allclose(np.abs(U[:, 0]), e3, atol=1e-15)
+    S = np.hstack([X0, U])
+    theta = np.linalg.eigvalsh(S.T @ A.to_dense() @ S)
+    np.testing.assert_allclose(theta, g["ritz_next"], atol=1e-14)
+
+
+def test_e1_plain_svqb_gives_spurious_ritz_value():
+    """Negative test: Algorithm 4 alone keeps four columns and a zero Ritz value."""
+    g, A, pen, X0 = _e1()
+    W0 = pen.A_mul(X0) - X0 * np.array(g["theta0"])
+    S = np.hstack([X0, W0])
+    U = L.svqb(S, S, 4 * L.EPS)
+    assert U.shape[1] == 4
+    theta = np.linalg.eigvalsh(U.T @ A.to_dense() @ U)
+    assert theta[0] < 1e-10 < 1.0 < theta[1]
+    assert np.linalg.norm(U.T @ U - np.eye(4)) > 0.5
+
+
+# ---------------------------------------------------------- contracts
+
+def _rand_metric(n, rng):
+    return rng.uniform(1, 2, n)
+
+
+def test_rayleigh_ritz_contract():
+    rng = np.random.default_rng(1)
+    n, m = 200, 9
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    b = _rand_metric(n, rng)
+    X = rng.standard_normal((n, m)) * np.logspace(0, 3, m)
+    C, theta = L.rayleigh_ritz(X.T @ A @ X, X.T @ (b[:, None] * X))
+    Y = X @ C
+    np.testing.assert_allclose(Y.T @ (b[:, None] * Y), np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(Y.T @ A @ Y, np.diag(theta), atol=1e-10)
+    assert np.all(np.diff(theta) >= 0)
+
+
+def test_rayleigh_ritz_breakdown_on_dependent_columns():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((50, 3))
+    X = np.hstack([X, X[:, :1]])
+    with pytest.raises(L.Breakdown):
+        L.rayleigh_ritz(X.T @ X, X.T @ X)
+
+
+@pytest.mark.parametrize("deficient", [False, True])
+def test_ortho_drop_contract(deficient):
+    rng = np.random.default_rng(2)
+    n = 300
+    b = _rand_metric(n, rng)
+    Bm = lambda Y: b[:, None] * Y
+    V0 = rng.standard_normal((n, 6))
+    C, _ = L.rayleigh_ritz(V0.T @ V0, V0.T @ Bm(V0))
+    V = V0 @ C
+    U0 = rng.standard_normal((n, 8))
+    if deficient:
+        U0 = np.hstack([U0, U0[:, :3] @ rng.standard_normal((3, 4)) + 1e-13 * rng.standard_normal((n, 4)),
+                        V[:, :2]])
+    U, BU = L.ortho_drop(Bm, U0, V, Bm(V), 100 * L.EPS)
+    k = U.shape[1]
+    assert k <= U0.shape[1]
+    # Algorithm 5's first inner pass (svqb with replacement) may keep roundoff
+    # directions as orthonormal columns, so only the contracts are pinned.
+    np.testing.assert_allclose(U.T @ Bm(U), np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(V.T @ Bm(U), 0, atol=1e-12)
+    # span([U, V]) contains span(U0) (up to the dropped roundoff directions)
+    Q = np.hstack([V, U])
+    proj = Q @ (Q.T @ Bm(U0))
+    rel = np.linalg.norm(U0 - proj, axis=0) / np.linalg.norm(U0, axis=0)
+    assert rel.max() < 1e-10
+
+
+def test_svqb_drop_span_equality():
+    rng = np.random.default_rng(3)
+    n = 100
+    U = rng.standard_normal((n, 5))
+    U = np.hstack([U, U @ rng.standard_normal((5, 2))])
+    out = L.svqb_drop(U, U, 7 * L.EPS)
+    assert out.shape[1] == 5
+    np.testing.assert_allclose(out.T @ out, np.eye(5), atol=1e-12)
+    np.testing.assert_allclose(out @ (out.T @ U), U, atol=1e-11)
+
+
+def _random_projected(rng, nx, np_, nw, orthonormal):
+    n = 400
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    b = rng.uniform(1, 2, n)
+    S = rng.standard_normal((n, nx + np_ + nw))
+    if orthonormal:
+        C, _ = L.rayleigh_ritz(S.T @ S, S.T @ (b[:, None] * S))
+        S = S @ C
+    return S.T @ A @ S, S.T @ (b[:, None] * S)
+
+
+@pytest.mark.parametrize("use_ortho,nc", [(False, 0), (False, 3), (True, 0), (True, 2)])
+def test_rayleigh_ritz_modified_contract(use_ortho, nc):
+    rng = np.random.default_rng(4)
+    nx, np_, nw = 8, 8 - nc, 8 - nc
+    SAS, SBS = _random_projected(rng, nx, np_, nw, use_ortho)
+    rr = L.rayleigh_ritz_modified(SAS, SBS, nx, nc, use_ortho)
+    assert not rr.flip
+    C = np.hstack([rr.Cx, rr.Cp])
+    assert C.shape == (nx + np_ + nw, 2 * nx - nc)
+    np.testing.assert_allclose(C.T @ SBS @ C, np.eye(2 * nx - nc), atol=1e-10)
+    G = C.T @ SAS @ C
+    np.testing.assert_allclose(G[:nx, :nx], np.diag(rr.theta), atol=1e-9)
+    np.testing.assert_allclose(G[:nx, nx:], 0, atol=1e-9)
+    np.testing.assert_allclose(G[nx:, nx:], rr.PAP, atol=1e-9)
+    # X is the Ritz block: the lowest n_x Ritz values of the pencil
+    w, _ = dense.pencil_eigh(SAS, SBS, use_jacobi=True)
+    np.testing.assert_allclose(rr.theta, w[:nx], atol=1e-9)
+
+
+def test_rayleigh_ritz_modified_flips_on_ill_conditioning():
+    rng = np.random.default_rng(5)
+    SAS, SBS = _random_projected(rng, 4, 0, 4, False)
+    # make the W block nearly dependent on X in the B metric
+    T = np.eye(8)
+    T[:4, 4:] = 1.0
+    T[4:, 4:] = 1e-7 * np.eye(4)
+    rr = L.rayleigh_ritz_modified(T.T @ SAS @ T, T.T @ SBS @ T, 4, 0, False)
+    assert rr.flip and rr.condR > 1e4
+
+
+def test_cp_reduces_to_lq_form_without_locking():
+    """With n_c = 0 the C_p reading spans the rows of Z_1perp (Sec. 4.2, LQ form)."""
+    rng = np.random.default_rng(6)
+    nx = 5
+    SAS, SBS = _random_projected(rng, nx, nx, nx, True)
+    rr = L.rayleigh_ritz_modified(SAS, SBS, nx, 0, True)
+    _, Z = np.linalg.eigh(SAS)
+    Z1p = Z[:nx, nx:]
+    Qt, _ = np.linalg.qr(Z1p.T)           # orthonormal basis of the rows of Z_1perp
+    Cp_lq = Z[:, nx:] @ Qt
+    # same column space
+    P1 = rr.Cp @ rr.Cp.T
+    P2 = Cp_lq @ Cp_lq.T
+    np.testing.assert_allclose(P1, P2, atol=1e-10)
+
+
+# ---------------------------------------------------------- convergence control
+
+def test_norm_estimate_bounds():
+    A = synth.laplacian_2d_dirichlet(20)
+    pen = _pencil(A)
+    Om = synth.normal_block(0, synth.STREAM_OMEGA, 16, A.n)
+    est = L.norm_estimate(pen.A_mul, Om)
+    true = np.linalg.norm(A.to_dense(), 2)
+    assert 0.3 * true < est <= true
+    I3 = synth.CSR(A.n, np.arange(A.n + 1, dtype=np.int32), np.arange(A.n, dtype=np.int32),
+                   np.full(A.n, -3.0))
+    assert abs(L.norm_estimate(_pencil(I3).A_mul, Om) - 3.0) < 1e-14
+
+
+def test_backward_error_scale_invariance_and_contrasts():
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((50, 3))
+    R = 1e-9 * rng.standard_normal((50, 3))
+    th = np.array([1e-14, 0.5, 2.0])
+    be = L.backward_error(R, X, th, 10.0, 1.0)
+    be2 = L.backward_error(5 * R, X, 5 * th / 0.5, 50.0, 0.5)  # (5A, 0.5B)
+    np.testing.assert_allclose(be, be2, rtol=1e-14)
+    # criterion (7) cannot be met for a ~1e-14 eigenvalue; (9) can
+    c7 = L.criterion7(R, X, th)
+    assert c7[0] > 1e-4 and be[0] < 1e-8
+    # criterion (8) with B scaled by 1e-10: passes trivially, (9) does not
+    Xb = X
+    BX = 1e-10 * Xb
+    Rb = rng.standard_normal((50, 3))
+    thb = np.array([1e10, 2e10, 3e10])
+    assert np.all(L.criterion8(Rb, Xb, BX, thb) < 1e-4)
+    assert np.all(L.backward_error(Rb, Xb, thb, 1.0, 1e-10) > 1e-4)
+
+
+# ---------------------------------------------------------- Algorithm 8
+
+@pytest.fixture(scope="module")
+def c1_run():
+    p = synth.make_problem("lap2d_32")
+    pen, r = _run(p)
+    return p, pen, r
+
+
+def test_c1_closed_form(c1_run):
+    p, pen, r = c1_run
+    assert r.status == L.OK
+    np.testing.assert_allclose(r.lam, p.closed_form[:8], rtol=1e-10)
+    assert np.all(r.be <= p.tol)
+    np.testing.assert_allclose(r.X.T @ r.X, np.eye(8), atol=1e-12)
+    np.testing.assert_allclose(r.X.T @ pen.A_mul(r.X), np.diag(r.lam), atol=1e-12)
+    # the returned backward errors are the true explicit ones of Eq. (9)
+    R = pen.A_mul(r.X) - r.X * r.lam
+    np.testing.assert_allclose(L.backward_error(R, r.X, r.lam, r.normA, r.normB), r.be,
+                               rtol=1e-6, atol=1e-15)
+    # Eq. (9) with the true 2-norm is at least as strict as with the estimate
+    assert r.normA <= 7.981887690292338 + 1e-12
+    assert 10 < r.iters < 400
+
+
+def test_c1_sign_normalisation(c1_run):
+    _, _, r = c1_run
+    idx = np.argmax(np.abs(r.X), axis=0)
+    assert np.all(r.X[idx, np.arange(8)] > 0)
+
+
+def test_brute_force_generalised_small():
+    rng_b = synth.uniform_block(3, synth.STREAM_BDIAG, 144, 1.0, 2.0)
+    A = synth.add_diagonal(synth.laplacian_2d_dirichlet(12),
+                           synth.uniform_block(3, synth.STREAM_POTENTIAL, 144))
+    p = synth.Problem("bf", A, 10, 1e-10, b_diag=rng_b, kdiag=A.diagonal())
+    pen, r = _run(p, seed=3)
+    assert r.status == L.OK
+    w, _ = dense.pencil_eigh(A.to_dense(), np.diag(rng_b))
+    np.testing.assert_allclose(r.lam, w[:10], rtol=1e-10)
+    np.testing.assert_allclose(r.X.T @ (rng_b[:, None] * r.X), np.eye(10), atol=1e-12)
+
+
+def test_scaling_invariance():
+    p = synth.make_problem("lap2d_32")
+    p.A = synth.laplacian_2d_dirichlet(16)
+    p.kdiag = p.A.diagonal()
+    p.k = 6
+    _, r1 = _run(p)
+    _, r2 = _run(p, scaleA=8.0, scaleB=0.25)
+    np.testing.assert_allclose(r2.lam, r1.lam * 32.0, rtol=1e-10)
+    assert abs(r1.iters - r2.iters) <= 1
+
+
+def test_direct_gram_mode_agrees():
+    p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
+    _, r1 = _run(p)
+    _, r2 = _run(p, opts=L.Options(direct_gram=True))
+    np.testing.assert_allclose(r1.lam, r2.lam, rtol=1e-10)
+
+
+def test_generalised_closed_form_b_constant():
+    p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
+    p.b_diag = np.full(p.A.n, 2.0)
+    _, r = _run(p)
+    ref = synth.problems.closed_form_laplacian((8, 8, 8), 6) / 2.0
+    np.testing.assert_allclose(r.lam, ref, rtol=1e-10)
+
+
+def test_forced_orthogonalisation_path():
+    """tau_skip = 1 forces the orthoDrop branch from the first iteration."""
+    p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
+    _, r = _run(p, opts=L.Options(tau_skip=1.0))
+    assert r.stats["flip_iter"] == 1 and r.stats["ortho_calls"] >= r.iters
+    _, r0 = _run(p)
+    np.testing.assert_allclose(r.lam, r0.lam, rtol=1e-10)
+
+
+def test_explicit_products_agree():
+    p = synth.make_problem("lap2d_32")
+    _, r1 = _run(p, opts=L.Options(implicit="never"))
+    np.testing.assert_allclose(r1.lam, p.closed_form[:8], rtol=1e-10)
+
+
+def test_periodic_hamiltonian_singular_a():
+    """V = 0: lambda_1 = 0 exactly; criterion (9) still converges."""
+    N = 6
+    A = synth.hamiltonian_3d_periodic(N, np.zeros(N ** 3))
+    p = synth.Problem("h0", A, 7, 1e-8, kdiag=None)
+    _, r = _run(p)
+    assert r.status == L.OK and abs(r.lam[0]) < 1e-12
+    j = np.arange(N)
+    one = 2.0 * np.sin(np.pi * j / N) ** 2
+    ref = np.sort((one[:, None, None] + one[None, :, None] + one[None, None, :]).ravel())
+    np.testing.assert_allclose(r.lam, ref[:7], atol=1e-10)
+
+
+def test_breakdown_and_not_converged():
+    A = synth.laplacian_2d_dirichlet(10)
+    pen = _pencil(A)
+    X0 = synth.normal_block(0, 1, A.n, 4)
+    X0[:, 3] = X0[:, 1]
+    Om = synth.normal_block(0, 5, 16, A.n)
+    assert L.lobpcg(pen, X0, 2, 1e-8, Om).status == L.BREAKDOWN
+    X0 = synth.normal_block(0, 1, A.n, 4)
+    r = L.lobpcg(pen, X0, 2, 1e-8, Om, L.Options(maxit=3))
+    assert r.status == L.NOT_CONVERGED and r.iters == 3
