@@ -1,0 +1,186 @@
+/*
+ * lobpcg.h -- C ABI of the GB300 robust LOBPCG library.
+ *
+ * Computes the k algebraically smallest eigenpairs of a sparse symmetric-
+ * definite pencil (A, B): A X = B X Lambda, X^T B X = I (Duersch, Shao, Yang,
+ * Gu, "A robust and efficient implementation of LOBPCG", 2018: Sec. 2, Eq. 1),
+ * with the robust iteration of Algorithm 8 of that paper.
+ *
+ * Conventions for every entry point:
+ *   - Return value: a lobpcg_status.  Nothing is thrown across the ABI.  After a
+ *     failure lobpcg_last_error() returns a message owned by the handle.
+ *   - Dense blocks are row-major with an explicit leading dimension (elements
+ *     between consecutive rows, >= the number of columns).  Small dense
+ *     matrices passed to the kernel-level entry points are column-major.
+ *   - Device pointers must point to memory of the current CUDA device.  Host
+ *     pointers may be pageable.  `stream` is a cudaStream_t (NULL: legacy
+ *     default stream); all device work of a call is ordered on that stream.
+ *   - Inputs are borrowed for the duration of the call; the handle copies what
+ *     it keeps.  Outputs go to caller-allocated buffers.
+ *   - A handle may be used by one host thread at a time.
+ *   - CSR matrices: int32 row pointers and column indices (nnz < 2^31), columns
+ *     sorted within a row, float64 values; A and B must be symmetric.
+ */
+#ifndef GB300_LOBPCG_H
+#define GB300_LOBPCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lobpcg_ctx* lobpcg_t;
+
+typedef enum {
+  LOBPCG_OK = 0,
+  LOBPCG_ERR_ARG = 1,            /* invalid argument (sizes, pointers, options) */
+  LOBPCG_ERR_NOT_CONVERGED = 2,  /* maxit reached; outputs hold the current iterate */
+  LOBPCG_ERR_BREAKDOWN = 3,      /* initial block numerically rank deficient (Alg. 2) */
+  LOBPCG_ERR_CUDA = 4,           /* a CUDA, cuBLAS or cuSOLVER call failed */
+  LOBPCG_ERR_OOM = 5,            /* device allocation failed */
+  LOBPCG_ERR_TIMEOUT = 6,        /* wall-clock limit of the options exceeded */
+  LOBPCG_ERR_CALLBACK = 7        /* the preconditioner callback returned non-zero */
+} lobpcg_status;
+
+typedef enum { LOBPCG_MEM_HOST = 0, LOBPCG_MEM_DEVICE = 1 } lobpcg_mem;
+
+/* Arithmetic used for the n-scaled dense contractions (Gram S^T Y and basis
+ * update S C).  Both give FP64-accurate results; see lobpcg_gram. */
+typedef enum {
+  LOBPCG_GEMM_F64 = 0,     /* plain FP64 fused multiply-add on the CUDA cores */
+  LOBPCG_GEMM_OZAKI = 1    /* FP64 emulated by exact BF16 splits on the tensor cores */
+} lobpcg_gemm_mode;
+
+/* Options; zero-initialise and set what you need, zeros select the defaults
+ * noted.  eps below is 2^-52. */
+typedef struct {
+  int64_t block_width;    /* n_x; 0: k + max(ceil(k/10), 2), the paper's ~10 % padding (Sec. 6) */
+  int32_t maxit;          /* 0: 2000 iterations (Sec. 6) */
+  int32_t implicit;       /* implicit product updates (Sec. 5.2): 0 auto (B = I or diagonal
+                             B with cond <= 1e4), 1 never, 2 always */
+  int32_t refresh_every;  /* 0: 50; explicit A X, A P recomputation period under implicit updates */
+  int32_t omega_rows;     /* 0: 16; rows s of the Gaussian sketch Omega of the norm estimates
+                             (Sec. 4.3).  Omega^T is the n x s block whose element (r, c) is
+                             normal number r*s + c of Philox stream 5 under the solve's seed */
+  int32_t gemm_mode;      /* lobpcg_gemm_mode; 0 selects LOBPCG_GEMM_F64 */
+  int32_t ozaki_slices;   /* 0: 6; BF16 slices per operand for LOBPCG_GEMM_OZAKI (3..7) */
+  int32_t certify;        /* 0: on; 1: off.  Explicit-product re-check of Eq. (9) at exit */
+  double tau_ortho;       /* 0: 100 eps; Algorithm 5 orthogonality tolerance */
+  double tau_skip;        /* 0: 100 eps; switch to orthogonalisation when cond(R)^-3 < tau_skip (Sec. 5.3) */
+  double max_seconds;     /* 0: no limit; host wall-clock limit -> LOBPCG_ERR_TIMEOUT */
+} lobpcg_options_t;
+
+/* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
+typedef struct {
+  int64_t iterations;
+  int64_t n_x;            /* block width used */
+  int64_t converged;      /* n_c at exit */
+  int64_t flip_iteration; /* iteration at which orthogonalisation switched on; -1 never */
+  int64_t ortho_calls;
+  int64_t svqb_passes;
+  int64_t dropped_columns;
+  int64_t gpu_launches;   /* kernels of this library launched by the last solve */
+  double norm_a, norm_b;  /* Gaussian-sketch norm estimates used in Eq. (9) */
+  double max_backward_error;
+  double ms_spmm, ms_gram, ms_update, ms_residual, ms_small_dense, ms_ortho, ms_total;
+} lobpcg_stats_t;
+
+/* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.
+ * R and W are device pointers with leading dimensions ldr, ldw; `stream` is the
+ * handle's cudaStream_t.  Return 0 on success; non-zero aborts the solve with
+ * LOBPCG_ERR_CALLBACK. */
+typedef int (*lobpcg_precond_fn)(void* ctx, int64_t n, int64_t ncols, const double* R,
+                                 int64_t ldr, double* W, int64_t ldw, void* stream);
+
+/* Create a handle bound to the current CUDA device and `stream`.  opts may be
+ * NULL (defaults).  The handle owns every device buffer it allocates. */
+int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, void* stream);
+
+/* Set the pencil.  A: CSR (n, A_nnz).  B: either CSR (B_rowptr != NULL), or a
+ * diagonal (B_diag != NULL, n values), or the identity (both NULL).  `mem`
+ * says whether the arrays are host or device pointers; they are copied.
+ * Resets the preconditioner to Jacobi K = diag(A) (Algorithm 1, line 7 / Eq. 2).
+ * Errors: LOBPCG_ERR_ARG for n <= 0, a zero diagonal entry of A (Jacobi), or
+ * nnz >= 2^31. */
+int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
+                        const int32_t* A_col, const double* A_val, int64_t A_nnz,
+                        const int32_t* B_rowptr, const int32_t* B_col,
+                        const double* B_val, int64_t B_nnz, const double* B_diag,
+                        int mem);
+
+/* Diagonal preconditioner K = diag(kdiag) (n values, `mem` as above);
+ * kdiag == NULL restores K = diag(A); a negative `mem` selects K = I. */
+int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int mem);
+
+/* General preconditioner through a callback (see lobpcg_precond_fn). */
+int lobpcg_set_precond_callback(lobpcg_t h, lobpcg_precond_fn fn, void* ctx);
+
+/* Algorithm 8: k smallest eigenpairs to backward error tol (Eq. 9).
+ *   X0      n x n_x initial block (row-major, leading dimension ldx0), or NULL:
+ *           standard normal entries from Philox4x32-10 with key `seed` and
+ *           stream 1 (element (r, c) is normal number r*n_x + c of the stream).
+ *   mem_in  memory kind of X0.
+ *   lambda  k eigenvalues, ascending (memory kind mem_out).
+ *   X       n x k eigenvectors, row-major with leading dimension ldx, B-
+ *           orthonormal, each sign-normalised so its largest-magnitude entry
+ *           (lowest index on ties) is positive.
+ *   iters   iterations of the main loop (host pointer, may be NULL).
+ *   resnorm k backward errors of Eq. (9) from explicit products (mem_out; may be NULL).
+ * Returns LOBPCG_ERR_NOT_CONVERGED (outputs valid) when maxit is reached. */
+int lobpcg_solve(lobpcg_t h, int64_t k, double tol, const double* X0, int64_t ldx0,
+                 uint64_t seed, int mem_in, double* lambda, double* X, int64_t ldx,
+                 int mem_out, int64_t* iters, double* resnorm);
+
+int lobpcg_get_stats(lobpcg_t h, lobpcg_stats_t* out);
+const char* lobpcg_last_error(lobpcg_t h);
+void lobpcg_destroy(lobpcg_t h);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level entry points: single steps of one iteration on device buffers,
+ * ordered on `stream`.  They allocate nothing unless noted.
+ * ------------------------------------------------------------------------- */
+
+/* Block sparse product Y = A X for an n x m row-major block X (the A W and
+ * B W products of Algorithm 8, Sec. 5.2), optionally also BY = diag(b) X
+ * (b != NULL).  All pointers are device pointers. */
+int lobpcg_spmm(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                const double* X, int64_t ldx, int64_t m, double* Y, int64_t ldy,
+                const double* b, double* BY, int64_t ldby, void* stream);
+
+/* Tall-skinny Gram G = U^T V (the block inner products of Sec. 5.2, Eq. 12-14):
+ * U n x p, V n x q row-major; G written column-major with leading dimension
+ * ldg (>= p).  mode: lobpcg_gemm_mode; `slices` is the Ozaki slice count (0:
+ * 6).  Needs device scratch; `work` of `work_bytes` bytes may be NULL, then
+ * the call allocates and frees its own (use lobpcg_gram_workspace to size it). */
+int lobpcg_gram(int64_t n, const double* U, int64_t ldu, int64_t p, const double* V,
+                int64_t ldv, int64_t q, double* G, int64_t ldg, int mode, int slices,
+                void* work, int64_t work_bytes, void* stream);
+int64_t lobpcg_gram_workspace(int64_t n, int64_t p, int64_t q, int mode, int slices);
+
+/* Basis update Y = beta * Y0 + alpha * S C (Eq. 10-11): S n x s row-major, C
+ * s x m column-major (leading dimension ldc), Y and Y0 n x m row-major (Y0 may
+ * be NULL when beta == 0; Y must not alias S).  mode/slices as lobpcg_gram. */
+int lobpcg_update(int64_t n, const double* S, int64_t lds, int64_t s, const double* C,
+                  int64_t ldc, int64_t m, double alpha, double beta, const double* Y0,
+                  int64_t ldy0, double* Y, int64_t ldy, int mode, int slices, void* stream);
+
+/* Residual, preconditioner and norms (Algorithm 8, lines 8-9 and 17-18):
+ * for columns j = c0 .. m-1: r_j = AX_j - theta_j BX_j (BX == NULL: B = I),
+ * W(:, j - c0) = r_j / kdiag (kdiag == NULL: K = I), and
+ * be_j = ||r_j|| / ((normA + |theta_j| normB) ||x_j||)  (Eq. 9) written to
+ * be[j - c0].  theta, kdiag, be: device pointers.  W may be NULL (norms only). */
+int lobpcg_residual(int64_t n, const double* X, const double* AX, const double* BX,
+                    int64_t ld, int64_t m, int64_t c0, const double* theta,
+                    const double* kdiag, double* W, int64_t ldw, double normA,
+                    double normB, double* be, void* stream);
+
+/* Philox4x32-10 normals: Y(r, c) = normal number r*m + c of stream `stream_id`
+ * under key `seed` (Box-Muller of two 52-bit uniforms), n x m row-major. */
+int lobpcg_philox_normal(int64_t n, int64_t m, uint64_t seed, uint32_t stream_id,
+                         double* Y, int64_t ldy, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LOBPCG_H */

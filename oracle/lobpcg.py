@@ -29,8 +29,10 @@ choice, identical in the CUDA library):
   * under soft locking C_p spans Z_perp * (Z_1perp^T Z_1(:, n_c+1:n_x)),
     orthonormalised by Householder QR (equivalently the LQ of its transpose);
     with n_c = 0 and Z_1 nonsingular this is the paper's Z_perp Q_1perp^T.
-  * columns whose B-norm squared is below the smallest normal double are
-    removed before the D scaling of svqb / svqbDrop (D is undefined there).
+  * a column whose B-norm squared is below the smallest normal double gets
+    D_jj = 0 in svqb / svqbDrop (the paper's D is undefined there): it then
+    spans a zero eigenvalue of D U^T B U D, which Algorithm 4 replaces (giving
+    a zero output column) and Algorithm 6 drops.
   * n_c is monotone: a locked column stays locked; locking is in order.
   * implicit updates of AX, AP are used when B = I or B is diagonal with
     cond(B) <= 1e4 (Sec. 5.2 safety rule), refreshed explicitly every 50
@@ -169,20 +171,23 @@ def rayleigh_ritz(GA, GB):
 # --------------------------------------------------------------------------
 # orthogonalisation (Algorithms 4, 5, 6)
 
-def _drop_zero_columns(U, G):
-    keep = np.diag(G) > np.finfo(np.float64).tiny
-    return U[:, keep], G[np.ix_(keep, keep)]
+def _scaling(G):
+    """D = diag(G)^-1/2, with D_jj = 0 for a column of zero B-norm."""
+    g = np.diag(G)
+    ok = g > np.finfo(np.float64).tiny
+    return np.where(ok, 1.0 / np.sqrt(np.where(ok, g, 1.0)), 0.0)
 
 
 def svqb(U, BU, tau_replace):
     """Algorithm 4: U D Z Theta^-1/2 with small theta replaced by tau*max|theta|."""
     G = U.T @ BU
     G = 0.5 * (G + G.T)
-    U, G = _drop_zero_columns(U, G)
     if U.shape[1] == 0:
         return U
-    d = 1.0 / np.sqrt(np.diag(G))
+    d = _scaling(G)
     theta, Z = dense.eigh(d[:, None] * G * d[None, :])
+    if not np.max(np.abs(theta)) > 0:
+        return U[:, :0]
     floor = tau_replace * np.max(np.abs(theta))
     theta = np.where(theta < floor, floor, theta)
     return U @ ((d[:, None] * Z) / np.sqrt(theta)[None, :])
@@ -192,10 +197,9 @@ def svqb_drop(U, BU, tau_drop):
     """Algorithm 6: keep J = {j : theta_j > tau_drop * max|theta|}."""
     G = U.T @ BU
     G = 0.5 * (G + G.T)
-    U, G = _drop_zero_columns(U, G)
     if U.shape[1] == 0:
         return U
-    d = 1.0 / np.sqrt(np.diag(G))
+    d = _scaling(G)
     theta, Z = dense.eigh(d[:, None] * G * d[None, :])
     J = theta > tau_drop * np.max(np.abs(theta))
     return U @ ((d[:, None] * Z[:, J]) / np.sqrt(theta[J])[None, :])

@@ -1,0 +1,150 @@
+"""GB300-native robust LOBPCG (Duersch, Shao, Yang, Gu, 2018; Algorithm 8).
+
+The solver and its kernels live in a CUDA shared library with a C ABI
+(include/lobpcg.h).  This package is only its binding:
+
+  _native   one Python function per C entry point, same names (ctypes)
+  Solver    convenience wrapper: create / set_operator / solve / stats
+
+PyTorch is used, when present, only to hand device buffers and streams to the
+library.  There is no CPU fallback: if the library is not built, importing the
+binding functions raises.
+"""
+import numpy as np
+
+from . import _native
+from ._native import (  # noqa: F401
+    LOBPCG_OK, LOBPCG_ERR_ARG, LOBPCG_ERR_NOT_CONVERGED, LOBPCG_ERR_BREAKDOWN,
+    LOBPCG_ERR_CUDA, LOBPCG_ERR_OOM, LOBPCG_ERR_TIMEOUT, LOBPCG_ERR_CALLBACK,
+    LOBPCG_MEM_HOST, LOBPCG_MEM_DEVICE, LOBPCG_GEMM_F64, LOBPCG_GEMM_OZAKI,
+    lobpcg_options_t, lobpcg_stats_t, LobpcgError,
+    lobpcg_create, lobpcg_set_operator, lobpcg_set_precond_diag,
+    lobpcg_set_precond_callback, lobpcg_solve, lobpcg_get_stats, lobpcg_last_error,
+    lobpcg_destroy, lobpcg_spmm, lobpcg_gram, lobpcg_gram_workspace, lobpcg_update,
+    lobpcg_residual, lobpcg_philox_normal, load, library_path,
+)
+
+__all__ = [n for n in dir() if n.startswith("lobpcg_") or n.startswith("LOBPCG_")] + [
+    "Solver", "options", "LobpcgError", "load", "library_path"]
+
+
+def options(**kw):
+    """lobpcg_options_t with the given fields set (zeros select defaults)."""
+    o = lobpcg_options_t()
+    for k, v in kw.items():
+        if k == "gemm_mode" and isinstance(v, str):
+            v = {"f64": LOBPCG_GEMM_F64, "ozaki": LOBPCG_GEMM_OZAKI}[v]
+        if k == "implicit" and isinstance(v, str):
+            v = {"auto": 0, "never": 1, "always": 2}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """Owning wrapper of one lobpcg_t handle.
+
+    Host arrays (numpy) or device tensors (torch, cuda) are accepted; the
+    memory kind is detected per argument group.
+    """
+
+    def __init__(self, stream=None, **opts):
+        self.opts = options(**opts)
+        self.stream = stream
+        self.h = lobpcg_create(self.opts, stream)
+        self.n = 0
+        self._cb = None
+
+    def close(self):
+        if self.h:
+            lobpcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def _mem(x):
+        if x is not None and hasattr(x, "is_cuda") and x.is_cuda:
+            return LOBPCG_MEM_DEVICE
+        return LOBPCG_MEM_HOST
+
+    def _check(self, rc, what):
+        if rc != LOBPCG_OK:
+            raise LobpcgError(rc, f"{what}: {lobpcg_last_error(self.h)}")
+
+    def set_operator(self, rowptr, col, val, b_diag=None, b_csr=None):
+        mem = self._mem(val)
+        n = len(rowptr) - 1
+        args = dict(B_diag=b_diag)
+        if b_csr is not None:
+            args = dict(B_rowptr=b_csr[0], B_col=b_csr[1], B_val=b_csr[2], B_nnz=len(b_csr[2]))
+        if mem == LOBPCG_MEM_HOST:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            if b_diag is not None:
+                args["B_diag"] = np.ascontiguousarray(b_diag, dtype=np.float64)
+        self._keep = (rowptr, col, val, args)
+        rc = lobpcg_set_operator(self.h, n, rowptr, col, val, len(val), mem=mem, **args)
+        self._check(rc, "set_operator")
+        self.n = n
+
+    def set_precond_diag(self, kdiag):
+        mem = self._mem(kdiag)
+        if kdiag is not None and mem == LOBPCG_MEM_HOST:
+            kdiag = np.ascontiguousarray(kdiag, dtype=np.float64)
+        self._check(lobpcg_set_precond_diag(self.h, kdiag, mem), "set_precond_diag")
+
+    def set_precond_identity(self):
+        self._check(lobpcg_set_precond_diag(self.h, None, -1), "set_precond_diag")
+
+    def set_precond_callback(self, fn):
+        """fn(n, ncols, R_ptr, ldr, W_ptr, ldw, stream_ptr) -> int (device pointers)."""
+        def tramp(ctx, n, ncols, R, ldr, W, ldw, stream):
+            try:
+                return int(fn(n, ncols, R, ldr, W, ldw, stream))
+            except Exception:
+                return 1
+        self._cb = _native.PRECOND_FN(tramp)
+        self._check(lobpcg_set_precond_callback(self.h, self._cb, None), "set_precond_callback")
+
+    def solve(self, k, tol=1e-8, X0=None, seed=0, device=False, raise_on_error=True):
+        """Return (lam, X, iters, backward_errors, status).
+
+        device=True returns torch CUDA tensors (outputs written in place by the
+        library); otherwise numpy arrays.
+        """
+        n = self.n
+        mem_in = self._mem(X0)
+        ldx0 = 0
+        if X0 is not None:
+            if mem_in == LOBPCG_MEM_HOST:
+                X0 = np.ascontiguousarray(X0, dtype=np.float64)
+            ldx0 = X0.shape[1]
+        if device:
+            import torch
+            lam = torch.empty(k, dtype=torch.float64, device="cuda")
+            X = torch.empty((n, k), dtype=torch.float64, device="cuda")
+            be = torch.empty(k, dtype=torch.float64, device="cuda")
+            mem_out = LOBPCG_MEM_DEVICE
+        else:
+            lam = np.empty(k)
+            X = np.empty((n, k))
+            be = np.empty(k)
+            mem_out = LOBPCG_MEM_HOST
+        rc, it = lobpcg_solve(self.h, k, tol, X0, ldx0, seed, mem_in, lam, X, k, mem_out, be)
+        if rc not in (LOBPCG_OK, LOBPCG_ERR_NOT_CONVERGED) and raise_on_error:
+            self._check(rc, "solve")
+        return lam, X, it, be, rc
+
+    def stats(self):
+        return lobpcg_get_stats(self.h).as_dict()

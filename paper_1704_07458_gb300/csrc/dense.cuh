@@ -1,0 +1,67 @@
+// Small dense layer (O(n_s^3) work on n_s x n_s matrices, column-major, FP64):
+// Rayleigh-Ritz (Algorithms 2 and 7), the svqb / svqbDrop transforms
+// (Algorithms 4 and 6) and the Frobenius tests of Algorithm 5.  Factorisations
+// run through cuSOLVER/cuBLAS on the device; the decisions that shape the next
+// step (Cholesky success, cond(R), how many columns survive) come back to the
+// host as a few scalars.
+#pragma once
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include "common.cuh"
+
+namespace lob {
+
+struct DenseLayer {
+  cudaStream_t st = nullptr;
+  cusolverDnHandle_t sol = nullptr;
+  cublasHandle_t blas = nullptr;
+  int64_t nmax = 0;
+  double* work = nullptr;
+  int lwork = 0;
+  int* info = nullptr;
+  double* A[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // nmax x nmax each
+  double* ev = nullptr;    // nmax
+  double* d = nullptr;     // nmax
+  double* tau = nullptr;   // nmax
+  double* scal = nullptr;  // 16 device scalars
+  double* host = nullptr;  // pinned host mirror, nmax + 64 doubles
+  int64_t launches = 0;
+
+  int init(cudaStream_t stream, int64_t n_max);
+  void release();
+};
+
+// Algorithm 2 on the Gram pair (GA, GB), nx x nx column-major (leading dim nx).
+// Writes C (nx x nx, leading dim nx) and theta (device, nx).  *breakdown is set
+// when the Cholesky factorisation fails or D GB D is numerically singular.
+int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double* C,
+               double* theta, bool* breakdown);
+
+// Algorithm 7.  SAS, SBS: ns x ns column-major (leading dim ns).  On success
+// writes C = [C_x, C_p] (ns x (nx + *npn), leading dim ns), theta (device, nx)
+// and PAP (npn x npn, leading dim npn).  *flip reports the switch to the
+// orthogonal branch (Cholesky failure or cond(R)^-3 < tau_skip).
+int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int nc,
+                bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
+                int* npn, double* theta, double* PAP);
+
+// svqb (drop == false, Algorithm 4) or svqbDrop (drop == true, Algorithm 6) on
+// the Gram G = U^T B U (nu x nu, leading dim nu): T = D Z(:, J) Theta(J)^-1/2,
+// written nu x *nkeep with leading dim nu.
+int svqb_transform(DenseLayer& L, const double* G, int nu, bool drop, double tau, double* T,
+                   int* nkeep);
+
+// Assemble the projected pencil on S = [X, P, W] from Theta, the saved P^T A P
+// (Eq. 14), the identities (12)-(13) and the W columns GAw = S^T A W,
+// GBw = S^T B W (ns x nw, leading dim ldgw; GBw == nullptr: S^T B S = I).
+int assemble(DenseLayer& L, int nx, int np, int nw, const double* theta, const double* PAP,
+             int ldpap, const double* GAw, const double* GBw, int ldgw, double* SAS,
+             double* SBS);
+
+// out[0] = ||G - I||_F (identity == true) or ||G||_F; out[1] = sum(a[0:na]);
+// out[2] = sum(b[0:nb]).  G: rows x cols, leading dim ldg.  Result to host.
+int small_stats(DenseLayer& L, const double* G, int rows, int cols, int ldg, bool identity,
+                const double* a, int na, const double* b, int nb, double out[3]);
+
+}  // namespace lob

@@ -1,0 +1,60 @@
+// Internal launchers of the n-scaled kernels (all device pointers, stream-ordered).
+#pragma once
+#include "common.cuh"
+
+namespace lob {
+
+// Y = A X (and BY = diag(b) X when b != nullptr); CSR A, X n x m row-major.
+int spmm(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* col,
+         const double* val, const double* X, int64_t ldx, int m, double* Y, int64_t ldy,
+         const double* b, double* BY, int64_t ldby);
+
+// G = U^T V (G column-major, leading dimension ldg), plain FP64 on the CUDA
+// cores with a split over rows and a fixed-order second pass (deterministic).
+int64_t gram_f64_workspace(int64_t n, int p, int q);
+int gram_f64(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
+             int64_t ldg, void* work, int64_t work_bytes);
+
+// G = U^T V with FP64 emulated through exact BF16 slices on the tensor cores.
+int64_t gram_ozaki_workspace(int64_t n, int p, int q, int slices);
+int gram_ozaki(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
+               int64_t ldg, int slices, void* work, int64_t work_bytes);
+
+// Y = beta * Y0 + alpha * S C; S segments (n x s), C s x m column-major.
+int update_f64(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc,
+               int m, double alpha, double beta, const SegList& Y0, const OutList& Y);
+int update_ozaki(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc,
+                 int m, double alpha, double beta, const SegList& Y0, const OutList& Y,
+                 int slices, void* work, int64_t work_bytes);
+int64_t update_ozaki_workspace(int64_t n, int s, int m, int slices);
+
+// Residual / preconditioner / Eq. (9) norms for columns c0..m-1.
+// partial: device scratch of residual_workspace(n, m) bytes.
+int64_t residual_workspace(int64_t n, int m);
+int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, const double* BX,
+             int64_t ld, int m, int c0, const double* theta, const double* kdiag, double* W,
+             int64_t ldw, double normA, double normB, double* be, void* partial);
+
+// Column sums of squares of an n x m block: out[j] = sum_i Y(i, j)^2 (fixed order).
+int64_t colsumsq_workspace(int64_t n, int m);
+int colsumsq(cudaStream_t st, int64_t n, const double* Y, int64_t ld, int m, double* out,
+             void* partial);
+
+// Y = diag(b) X (n x m).
+int diag_scale(cudaStream_t st, int64_t n, int m, const double* b, const double* X,
+               int64_t ldx, double* Y, int64_t ldy);
+
+// Philox4x32-10 normals (see lobpcg_philox_normal).
+int philox_normal(cudaStream_t st, int64_t n, int m, uint64_t seed, uint32_t stream_id,
+                  double* Y, int64_t ldy);
+
+// Copy an n x m row-major block between leading dimensions (device to device).
+int copy_block(cudaStream_t st, int64_t n, int m, const double* X, int64_t ldx, double* Y,
+               int64_t ldy);
+
+// Sign normalisation: flip column j so its largest-|.| entry (lowest row on ties)
+// is positive.  work: 2 * m * 152 doubles + m ints of scratch.
+int sign_normalise(cudaStream_t st, int64_t n, int m, double* X, int64_t ldx, void* work);
+int64_t sign_normalise_workspace(int64_t n, int m);
+
+}  // namespace lob

@@ -1,0 +1,829 @@
+// Host driver of the robust LOBPCG (Algorithm 8 of Duersch, Shao, Yang, Gu,
+// 2018) and the solver half of the C ABI.
+//
+// Every n-scaled step runs in this library's kernels (spmm.cu, blas.cu,
+// ozaki.cu); the O(n_s^3) Rayleigh-Ritz work runs in dense.cu.  The host only
+// keeps the control flow: the shapes of the next step depend on a few scalars
+// (Cholesky success, cond(R), surviving columns, the number of converged
+// pairs) that come back once or a few times per iteration.
+//
+// Device layout: every n x . block (X, P, W, AX, AP, AW, BX, BP, BW and their
+// next-iteration copies) is a separate row-major n x ld buffer, ld = n_x
+// rounded up to 8 doubles (64 bytes).  S = [X, P, W] is never materialised:
+// the kernels take it as a list of column segments.  The update of Eq. (10)
+// writes into the "next" buffers and the pointers swap (ping-pong), which
+// the paper's row-chunked in-place scheme of Eq. (11) needs no workspace for.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dense.cuh"
+#include "kernels.cuh"
+
+using namespace lob;
+
+namespace {
+constexpr double kEps = 2.220446049250313e-16;
+
+enum Phase { PH_SPMM, PH_GRAM, PH_UPDATE, PH_RESID, PH_DENSE, PH_ORTHO, PH_COUNT };
+
+struct PhaseTimer {
+  // Nesting-safe: a phase's time includes the phases opened inside it.
+  std::vector<cudaEvent_t> pool;
+  struct Mark { int phase; int e0, e1; };
+  std::vector<Mark> marks;
+  std::vector<std::pair<int, int>> open;  // (phase, start event) stack
+  size_t used = 0;
+  double total[PH_COUNT] = {0};
+  cudaStream_t st = nullptr;
+  int ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[used], st);
+    return (int)used++;
+  }
+  void begin(int ph) { open.push_back({ph, ev()}); }
+  void end() {
+    const auto top = open.back();
+    open.pop_back();
+    marks.push_back({top.first, top.second, ev()});
+  }
+  // Call only after a stream synchronisation with no phase open.
+  void flush() {
+    for (auto& m : marks) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pool[m.e0], pool[m.e1]) == cudaSuccess) total[m.phase] += ms;
+    }
+    marks.clear();
+    if (open.empty()) used = 0;
+  }
+  void reset() {
+    flush();
+    open.clear();
+    used = 0;
+    for (auto& t : total) t = 0;
+  }
+  ~PhaseTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct Scoped {
+  PhaseTimer& t;
+  Scoped(PhaseTimer& tm, int ph) : t(tm) { t.begin(ph); }
+  ~Scoped() { t.end(); }
+};
+}  // namespace
+
+struct lobpcg_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  lobpcg_options_t opt{};
+  std::string err;
+  lobpcg_stats_t stats{};
+  // operator
+  int64_t n = 0, A_nnz = 0, B_nnz = 0;
+  int32_t *A_rp = nullptr, *A_ci = nullptr, *B_rp = nullptr, *B_ci = nullptr;
+  double *A_v = nullptr, *B_v = nullptr, *b_diag = nullptr;
+  int b_kind = 0;  // 0 identity, 1 diagonal, 2 CSR
+  double b_cond = 1.0;
+  int k_kind = 0;  // 0 diag(A), 1 user diagonal, 2 identity, 3 callback
+  double *adiag = nullptr, *kdiag = nullptr;
+  lobpcg_precond_fn cb = nullptr;
+  void* cb_ctx = nullptr;
+  // workspace of the current shape
+  std::vector<void*> ws;
+  int64_t ws_n = -1, ws_nx = -1;
+  int ws_b = -1, ws_mode = -1, ws_slices = -1;
+  int64_t ld = 0;
+  double *X, *P, *AX, *AP, *AW, *BX, *BP, *BW, *Xn, *Pn, *AXn, *APn, *BXn, *BPn, *Om;
+  double* wbuf[4];
+  double *theta, *be, *colA, *colB, *Gw, *Gs, *SAS, *SBS, *Cm, *PAP, *PAPn;
+  void* gwork = nullptr;
+  int64_t gwork_bytes = 0;
+  void* uwork = nullptr;
+  int64_t uwork_bytes = 0;
+  void* rwork = nullptr;
+  double* hbuf = nullptr;  // pinned host
+  DenseLayer dense;
+  PhaseTimer timer;
+
+  ~lobpcg_ctx() { release_all(); }
+
+  void free_ws() {
+    for (void* p : ws) cudaFree(p);
+    ws.clear();
+    ws_n = ws_nx = -1;
+  }
+  void release_op() {
+    for (void** p : {(void**)&A_rp, (void**)&A_ci, (void**)&A_v, (void**)&B_rp, (void**)&B_ci,
+                     (void**)&B_v, (void**)&b_diag, (void**)&adiag, (void**)&kdiag}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
+  }
+  void release_all() {
+    free_ws();
+    release_op();
+    dense.release();
+    if (hbuf) cudaFreeHost(hbuf);
+    hbuf = nullptr;
+  }
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+};
+
+namespace {
+
+int dalloc(lobpcg_ctx* h, void** p, size_t bytes) {
+  if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    return LOBPCG_ERR_OOM;
+  }
+  h->ws.push_back(*p);
+  return LOBPCG_OK;
+}
+
+int gemm_mode(const lobpcg_ctx* h) { return h->opt.gemm_mode == LOBPCG_GEMM_OZAKI ? 1 : 0; }
+int slices(const lobpcg_ctx* h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : 6; }
+
+int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
+  const int64_t n = h->n;
+  if (h->ws_n == n && h->ws_nx == nx && h->ws_b == h->b_kind && h->ws_mode == gemm_mode(h) &&
+      h->ws_slices == slices(h))
+    return LOBPCG_OK;
+  h->free_ws();
+  const int s = h->opt.omega_rows > 0 ? h->opt.omega_rows : 16;
+  h->ld = round_up(std::max<int64_t>(nx, s), 8);
+  const size_t blk = (size_t)n * h->ld * sizeof(double);
+  int rc;
+  double** blocks[] = {&h->X, &h->P, &h->AX, &h->AP, &h->AW, &h->Xn, &h->Pn, &h->AXn, &h->APn,
+                       &h->wbuf[0], &h->wbuf[1], &h->wbuf[2], &h->wbuf[3], &h->Om};
+  for (double** b : blocks)
+    if ((rc = dalloc(h, (void**)b, blk))) return rc;
+  if (h->b_kind != 0) {
+    double** bb[] = {&h->BX, &h->BP, &h->BW, &h->BXn, &h->BPn};
+    for (double** b : bb)
+      if ((rc = dalloc(h, (void**)b, blk))) return rc;
+  } else {
+    h->BX = h->BP = h->BW = h->BXn = h->BPn = nullptr;
+  }
+  const int64_t nsmax = 3 * nx;
+  const size_t sm = (size_t)nsmax * nsmax * sizeof(double);
+  double** smalls[] = {&h->Gw, &h->Gs, &h->SAS, &h->SBS, &h->Cm, &h->PAP, &h->PAPn};
+  for (double** b : smalls)
+    if ((rc = dalloc(h, (void**)b, 2 * sm))) return rc;
+  double** vecs[] = {&h->theta, &h->be, &h->colA, &h->colB};
+  for (double** b : vecs)
+    if ((rc = dalloc(h, (void**)b, (size_t)std::max<int64_t>(nsmax, s) * 2 * sizeof(double))))
+      return rc;
+  // Gram scratch: the widest use is S^T [AW, BW] (3 nx x 2 nx) or X^T [AX, BX].
+  const int mode = gemm_mode(h), sl = slices(h);
+  // The slab count depends on the shape, so take the maximum over every Gram
+  // shape the driver can request (p <= 3 n_x, q <= 2 n_x).
+  int64_t gb = 0;
+  for (int p = 1; p <= nsmax; ++p)
+    for (int q = 1; q <= 2 * nx; ++q) {
+      gb = std::max(gb, gram_f64_workspace(n, p, q));
+      if (mode) gb = std::max(gb, gram_ozaki_workspace(n, p, q, sl));
+    }
+  h->gwork_bytes = gb;
+  if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
+  h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), sl) : 0;
+  if (h->uwork_bytes > 0 && (rc = dalloc(h, &h->uwork, (size_t)h->uwork_bytes))) return rc;
+  const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
+  if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
+  if ((rc = h->dense.init(h->st, nsmax))) return rc;
+  h->ws_n = n;
+  h->ws_nx = nx;
+  h->ws_b = h->b_kind;
+  h->ws_mode = mode;
+  h->ws_slices = sl;
+  return LOBPCG_OK;
+}
+
+// ---- thin wrappers choosing the arithmetic of the dense contractions
+
+int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t ldg) {
+  if (gemm_mode(h))
+    return gram_ozaki(h->st, h->n, U, V, G, ldg, slices(h), h->gwork, h->gwork_bytes);
+  return gram_f64(h->st, h->n, U, V, G, ldg, h->gwork, h->gwork_bytes);
+}
+
+int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m, double alpha,
+           double beta, const SegList& Y0, const OutList& Y) {
+  if (gemm_mode(h))
+    return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y, slices(h), h->uwork,
+                        h->uwork_bytes);
+  return update_f64(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y);
+}
+
+OutList out1(double* p, int64_t ld, int m) { return OutList{{p, p}, {ld, ld}, m}; }
+
+// Y = A X (and BY = B X when by != nullptr and B is not the identity)
+int apply_AB(lobpcg_ctx* h, const double* X, int m, double* AY, double* BY) {
+  if (m <= 0) return LOBPCG_OK;
+  Scoped sc(h->timer, PH_SPMM);
+  int rc = spmm(h->st, h->n, h->A_rp, h->A_ci, h->A_v, X, h->ld, m, AY, h->ld,
+                (BY && h->b_kind == 1) ? h->b_diag : nullptr, BY, h->ld);
+  if (rc || !BY) return rc;
+  if (h->b_kind == 2)
+    rc = spmm(h->st, h->n, h->B_rp, h->B_ci, h->B_v, X, h->ld, m, BY, h->ld, nullptr, nullptr, 0);
+  return rc;
+}
+
+int apply_B(lobpcg_ctx* h, const double* X, int m, double* BY) {
+  if (m <= 0 || h->b_kind == 0) return LOBPCG_OK;
+  Scoped sc(h->timer, PH_SPMM);
+  if (h->b_kind == 1) return diag_scale(h->st, h->n, m, h->b_diag, X, h->ld, BY, h->ld);
+  return spmm(h->st, h->n, h->B_rp, h->B_ci, h->B_v, X, h->ld, m, BY, h->ld, nullptr, nullptr, 0);
+}
+
+int to_host(lobpcg_ctx* h, double* dst, const double* src, int64_t count) {
+  if (count <= 0) return LOBPCG_OK;
+  LOB_CUDA_OK(cudaMemcpyAsync(h->hbuf, src, count * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LOB_CUDA_OK(cudaStreamSynchronize(h->st));
+  memcpy(dst, h->hbuf, count * sizeof(double));
+  h->timer.flush();
+  return LOBPCG_OK;
+}
+
+int sum_sq_norms(lobpcg_ctx* h, const double* Y, int m, double* out) {
+  // out = sum of squares of an n x m block
+  int rc = colsumsq(h->st, h->n, Y, h->ld, m, h->colA, h->rwork);
+  if (rc) return rc;
+  double s[3];
+  if ((rc = small_stats(h->dense, h->Gs, 0, 0, 1, false, h->colA, m, h->colA, 0, s))) return rc;
+  *out = s[1];
+  return LOBPCG_OK;
+}
+
+int64_t leading_converged(const double* be, int64_t m, double tol) {
+  int64_t i = 0;
+  while (i < m && be[i] <= tol) ++i;
+  return i;
+}
+
+// Algorithm 5 (orthoDrop) with M = B on the active W columns.  U points at the
+// active block (inside one of the wbuf buffers); the result may move to another
+// buffer.  V = [X, P] with BV = [BX, BP].
+int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int np,
+               double tau_ortho) {
+  Scoped sc(h->timer, PH_ORTHO);
+  h->stats.ortho_calls++;
+  const int nin = nu;
+  auto spare = [&](const double* a, const double* b) {
+    for (double* w : h->wbuf)
+      if (w != a && w != b) return w;
+    return (double*)nullptr;
+  };
+  const double* BXp = h->b_kind ? h->BX : h->X;
+  const double* BPp = h->b_kind ? h->BP : h->P;
+  SegList V = seg_empty();
+  seg_push(V, h->X, h->ld, nx);
+  seg_push(V, h->P, h->ld, np);
+  SegList BV = seg_empty();
+  seg_push(BV, BXp, h->ld, nx);
+  seg_push(BV, BPp, h->ld, np);
+  const int nv = nx + np;
+  int rc;
+  double nbv = 0.0, t;
+  if ((rc = sum_sq_norms(h, BXp, nx, &nbv))) return rc;
+  if (np > 0) {
+    if ((rc = sum_sq_norms(h, BPp, np, &t))) return rc;
+    nbv += t;
+  }
+  nbv = std::sqrt(nbv);
+  double* BU = h->b_kind ? h->BW : nullptr;
+  double st3[3];
+  for (int i = 0; i < 3 && nu > 0; ++i) {
+    // U = U - V (V^T B U), with V^T B U formed as (BV)^T U
+    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv))) return rc;
+    double* dst = spare(Ubase, nullptr);
+    if ((rc = update(h, V, h->Gs, nv, nu, -1.0, 1.0, seg1(U, h->ld, nu), out1(dst, h->ld, nu))))
+      return rc;
+    U = Ubase = dst;
+    for (int j = 0; j < 3; ++j) {
+      const double* BUp = U;
+      if (h->b_kind) {
+        if ((rc = apply_B(h, U, nu, BU))) return rc;
+        BUp = BU;
+      }
+      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu))) return rc;
+      int keep = 0;
+      {
+        Scoped sd(h->timer, PH_DENSE);
+        if ((rc = svqb_transform(h->dense, h->Gs, nu, j > 0, nu * kEps, h->Cm, &keep))) return rc;
+      }
+      h->stats.svqb_passes++;
+      if (keep == 0) {
+        nu = 0;
+        break;
+      }
+      dst = spare(Ubase, nullptr);
+      if ((rc = update(h, seg1(U, h->ld, nu), h->Cm, nu, keep, 1.0, 0.0, seg_empty(),
+                       out1(dst, h->ld, keep))))
+        return rc;
+      U = Ubase = dst;
+      nu = keep;
+      BUp = U;
+      if (h->b_kind) {
+        if ((rc = apply_B(h, U, nu, BU))) return rc;
+        BUp = BU;
+      }
+      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu))) return rc;
+      if ((rc = colsumsq(h->st, h->n, U, h->ld, nu, h->colA, h->rwork))) return rc;
+      if ((rc = colsumsq(h->st, h->n, BUp, h->ld, nu, h->colB, h->rwork))) return rc;
+      if ((rc = small_stats(h->dense, h->Gs, nu, nu, nu, true, h->colA, nu, h->colB, nu, st3)))
+        return rc;
+      const double err = st3[0] / (std::sqrt(st3[2]) * std::sqrt(st3[1]));
+      if (err <= tau_ortho) break;
+    }
+    if (nu == 0 || nv == 0) break;
+    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv))) return rc;
+    if ((rc = colsumsq(h->st, h->n, U, h->ld, nu, h->colA, h->rwork))) return rc;
+    if ((rc = small_stats(h->dense, h->Gs, nv, nu, nv, false, h->colA, nu, h->colA, 0, st3)))
+      return rc;
+    const double err = st3[0] / (nbv * std::sqrt(st3[1]));
+    if (err <= tau_ortho) break;
+  }
+  h->stats.dropped_columns += nin - nu;
+  return LOBPCG_OK;
+}
+
+int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t ldx0,
+               uint64_t seed, int mem_in, double* lambda, double* Xout, int64_t ldx,
+               int mem_out, int64_t* iters, double* resnorm) {
+  const int64_t n = h->n;
+  if (n <= 0) return h->fail(LOBPCG_ERR_ARG, "no operator set");
+  if (k <= 0 || k > n) return h->fail(LOBPCG_ERR_ARG, "k must be in 1..n");
+  if (!(tol > 0)) return h->fail(LOBPCG_ERR_ARG, "tol must be positive");
+  int64_t nx = h->opt.block_width > 0 ? h->opt.block_width
+                                      : k + std::max<int64_t>((k + 9) / 10, 2);
+  nx = std::min(nx, n);
+  if (nx < k) return h->fail(LOBPCG_ERR_ARG, "block_width < k");
+  if (3 * nx > 65536) return h->fail(LOBPCG_ERR_ARG, "block too wide");
+  if (!lambda || !Xout || ldx < k) return h->fail(LOBPCG_ERR_ARG, "bad output buffers");
+  if (X0 && ldx0 < nx) return h->fail(LOBPCG_ERR_ARG, "ldx0 < block width");
+  if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
+  int rc = ensure_workspace(h, nx);
+  if (rc) return h->fail(rc, "workspace allocation failed");
+  const auto t_start = std::chrono::steady_clock::now();
+  const int64_t launches0 = g_launches;
+  h->timer.st = h->st;
+  h->timer.reset();
+  h->stats = lobpcg_stats_t{};
+  h->stats.n_x = nx;
+  h->stats.flip_iteration = -1;
+  const int64_t ld = h->ld;
+  const int s = h->opt.omega_rows > 0 ? h->opt.omega_rows : 16;
+  const int maxit = h->opt.maxit > 0 ? h->opt.maxit : 2000;
+  const double tau_ortho = h->opt.tau_ortho > 0 ? h->opt.tau_ortho : 100 * kEps;
+  const double tau_skip = h->opt.tau_skip > 0 ? h->opt.tau_skip : 100 * kEps;
+  const int refresh_every = h->opt.refresh_every > 0 ? h->opt.refresh_every : 50;
+  bool implicit = h->b_kind == 0 || (h->b_kind == 1 && h->b_cond <= 1e4);
+  if (h->opt.implicit == 1) implicit = false;
+  if (h->opt.implicit == 2) implicit = true;
+  const double* kd = (h->k_kind == 0) ? h->adiag : (h->k_kind == 1 ? h->kdiag : nullptr);
+  std::vector<double> be_h(std::max<int64_t>(nx, s) + 8), th_h(nx);
+
+  // ---- Sec. 4.3: Gaussian-sketch norm estimates ||M||^(Omega) = ||M Omega^T||_F / ||Omega||_F
+  if ((rc = philox_normal(h->st, n, s, seed, 5u, h->Om, ld))) return rc;
+  double om2, am2, bm2 = 1.0;
+  if ((rc = sum_sq_norms(h, h->Om, s, &om2))) return rc;
+  double* tmp = h->wbuf[0];
+  if ((rc = apply_AB(h, h->Om, s, tmp, nullptr))) return rc;
+  if ((rc = sum_sq_norms(h, tmp, s, &am2))) return rc;
+  const double normA = std::sqrt(am2 / om2);
+  double normB = 1.0;
+  if (h->b_kind) {
+    if ((rc = apply_B(h, h->Om, s, tmp))) return rc;
+    if ((rc = sum_sq_norms(h, tmp, s, &bm2))) return rc;
+    normB = std::sqrt(bm2 / om2);
+  }
+  h->stats.norm_a = normA;
+  h->stats.norm_b = normB;
+
+  // ---- Algorithm 8, lines 3-6: X = X0 C with [C, Theta] = RayleighRitz(X0)
+  if (X0) {
+    LOB_CUDA_OK(cudaMemcpy2DAsync(h->X, ld * sizeof(double), X0, ldx0 * sizeof(double),
+                                  nx * sizeof(double), n,
+                                  mem_in == LOBPCG_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                              : cudaMemcpyHostToDevice,
+                                  h->st));
+  } else if ((rc = philox_normal(h->st, n, (int)nx, seed, 1u, h->X, ld))) {
+    return rc;
+  }
+  double* BXp = h->b_kind ? h->BX : h->X;
+  if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
+  {
+    Scoped sc(h->timer, PH_GRAM);
+    SegList V = seg_empty();
+    seg_push(V, h->AX, ld, (int)nx);
+    seg_push(V, BXp, ld, (int)nx);
+    if ((rc = gram(h, seg1(h->X, ld, (int)nx), V, h->Gw, nx))) return rc;
+  }
+  bool breakdown = false;
+  {
+    Scoped sc(h->timer, PH_DENSE);
+    if ((rc = rr_initial(h->dense, h->Gw, h->Gw + nx * nx, (int)nx, h->Cm, h->theta, &breakdown)))
+      return rc;
+  }
+  if (breakdown) return h->fail(LOBPCG_ERR_BREAKDOWN, "initial block is rank deficient");
+  {
+    Scoped sc(h->timer, PH_UPDATE);
+    if ((rc = update(h, seg1(h->X, ld, (int)nx), h->Cm, nx, (int)nx, 1.0, 0.0, seg_empty(),
+                     out1(h->Xn, ld, (int)nx))))
+      return rc;
+  }
+  std::swap(h->X, h->Xn);
+  BXp = h->b_kind ? h->BX : h->X;
+  if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
+
+  int64_t nc = 0;
+  int np = 0;
+  bool use_ortho = false, refresh_next = false;
+  int64_t it = 0;
+  int status = LOBPCG_OK;
+  // W (or R for a callback preconditioner) of columns c0 .. nx-1, then locking.
+  double* Wbase = h->wbuf[0];
+  double* Wp = Wbase;
+  auto residual_step = [&](int64_t c0, bool write_w) -> int {
+    Scoped sc(h->timer, PH_RESID);
+    const double* bx = h->b_kind ? h->BX : nullptr;
+    double* dst = nullptr;
+    if (write_w) dst = (h->k_kind == 3) ? h->wbuf[3] : Wbase;
+    int r = residual(h->st, n, h->X, h->AX, bx, ld, (int)nx, (int)c0, h->theta,
+                     (h->k_kind == 3) ? nullptr : kd, dst, ld, normA, normB, h->be, h->rwork);
+    return r;
+  };
+  auto finish_w = [&](int64_t c0, int64_t ncn) -> int {
+    // active W columns ncn .. nx-1 of a residual written from column c0
+    const int64_t off = ncn - c0;
+    if (h->k_kind == 3) {
+      const int64_t nw = nx - ncn;
+      if (nw > 0 && h->cb(h->cb_ctx, n, nw, h->wbuf[3] + off, ld, Wbase, ld, (void*)h->st) != 0)
+        return LOBPCG_ERR_CALLBACK;
+      Wp = Wbase;
+    } else {
+      Wp = Wbase + off;
+    }
+    return LOBPCG_OK;
+  };
+  Wbase = h->wbuf[0];
+  if ((rc = residual_step(0, true))) return rc;
+  if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
+  nc = std::min<int64_t>(leading_converged(be_h.data(), nx, tol), nx);
+  if ((rc = finish_w(0, nc))) return h->fail(rc, "preconditioner callback failed");
+
+  for (;;) {
+    while (nc < k) {
+      if (it >= maxit) {
+        status = LOBPCG_ERR_NOT_CONVERGED;
+        break;
+      }
+      if (h->opt.max_seconds > 0 &&
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() >
+              h->opt.max_seconds) {
+        status = LOBPCG_ERR_TIMEOUT;
+        break;
+      }
+      ++it;
+      int nw = (int)(nx - nc);
+      const bool need_sbs = true;
+      // W-products, Gram of the W columns, projected pencil, Algorithm 7
+      auto project = [&](bool ortho, double* SASo, double* SBSo) -> int {
+        int r;
+        double* BWp = h->b_kind ? h->BW : Wp;
+        if ((r = apply_AB(h, Wp, nw, h->AW, h->b_kind ? h->BW : nullptr))) return r;
+        const int ns = (int)nx + np + nw;
+        SegList S = seg_empty();
+        seg_push(S, h->X, ld, (int)nx);
+        seg_push(S, h->P, ld, np);
+        seg_push(S, Wp, ld, nw);
+        SegList V = seg_empty();
+        seg_push(V, h->AW, ld, nw);
+        if (!ortho && need_sbs) seg_push(V, BWp, ld, nw);
+        {
+          Scoped sc(h->timer, PH_GRAM);
+          if ((r = gram(h, S, V, h->Gw, ns))) return r;
+        }
+        Scoped sd(h->timer, PH_DENSE);
+        return assemble(h->dense, (int)nx, np, nw, h->theta, h->PAP, np, h->Gw,
+                        ortho ? nullptr : h->Gw + (int64_t)ns * nw, ns, SASo, SBSo);
+      };
+      if (use_ortho) {
+        if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
+      }
+      if ((rc = project(use_ortho, h->SAS, h->SBS))) return rc;
+      int ns = (int)nx + np + nw;
+      bool flip = false;
+      double condR = 1.0;
+      int npn = 0;
+      {
+        Scoped sd(h->timer, PH_DENSE);
+        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, (int)nc, use_ortho, tau_skip,
+                              &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
+          return rc;
+      }
+      if (flip) {
+        // Algorithm 8, lines 12-15
+        use_ortho = true;
+        h->stats.flip_iteration = it;
+        if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
+        if ((rc = project(true, h->SAS, h->SBS))) return rc;
+        ns = (int)nx + np + nw;
+        Scoped sd(h->timer, PH_DENSE);
+        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, (int)nc, true, tau_skip,
+                              &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
+          return rc;
+      }
+      // Algorithm 8, line 16 and Sec. 5.2: [X, P] = S [C_x, C_p] (+ implicit products)
+      const int mo = (int)nx + npn;
+      const bool refresh = refresh_next || (it % refresh_every == 0);
+      {
+        Scoped sc(h->timer, PH_UPDATE);
+        SegList S = seg_empty();
+        seg_push(S, h->X, ld, (int)nx);
+        seg_push(S, h->P, ld, np);
+        seg_push(S, Wp, ld, nw);
+        OutList O{{h->Xn, h->Pn}, {ld, ld}, (int)nx};
+        if ((rc = update(h, S, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), O))) return rc;
+        if (implicit && !refresh) {
+          SegList AS = seg_empty();
+          seg_push(AS, h->AX, ld, (int)nx);
+          seg_push(AS, h->AP, ld, np);
+          seg_push(AS, h->AW, ld, nw);
+          OutList AO{{h->AXn, h->APn}, {ld, ld}, (int)nx};
+          if ((rc = update(h, AS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), AO))) return rc;
+          if (h->b_kind == 2) {
+            SegList BS = seg_empty();
+            seg_push(BS, h->BX, ld, (int)nx);
+            seg_push(BS, h->BP, ld, np);
+            seg_push(BS, h->BW, ld, nw);
+            OutList BO{{h->BXn, h->BPn}, {ld, ld}, (int)nx};
+            if ((rc = update(h, BS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), BO))) return rc;
+          }
+        }
+      }
+      if (!(implicit && !refresh)) {
+        if ((rc = apply_AB(h, h->Xn, (int)nx, h->AXn, h->b_kind ? h->BXn : nullptr))) return rc;
+        if ((rc = apply_AB(h, h->Pn, npn, h->APn, h->b_kind ? h->BPn : nullptr))) return rc;
+      } else if (h->b_kind == 1) {
+        if ((rc = apply_B(h, h->Xn, (int)nx, h->BXn))) return rc;
+        if ((rc = apply_B(h, h->Pn, npn, h->BPn))) return rc;
+      }
+      std::swap(h->X, h->Xn);
+      std::swap(h->P, h->Pn);
+      std::swap(h->AX, h->AXn);
+      std::swap(h->AP, h->APn);
+      std::swap(h->BX, h->BXn);
+      std::swap(h->BP, h->BPn);
+      std::swap(h->PAP, h->PAPn);
+      np = npn;
+      // Algorithm 8, lines 17-18
+      Wbase = (Wbase == h->wbuf[0]) ? h->wbuf[1] : h->wbuf[0];
+      if ((rc = residual_step(nc, true))) return rc;
+      if ((rc = to_host(h, be_h.data(), h->be, nx - nc))) return rc;
+      const int64_t ncn = std::max(nc, nc + leading_converged(be_h.data(), nx - nc, tol));
+      refresh_next = ncn > nc;
+      if ((rc = finish_w(nc, ncn))) return h->fail(rc, "preconditioner callback failed");
+      nc = ncn;
+    }
+    if (status != LOBPCG_OK || h->opt.certify == 1) break;
+    // exit certification: explicit products and Eq. (9) again
+    if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
+    if ((rc = residual_step(0, false))) return rc;
+    if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
+    const int64_t good = leading_converged(be_h.data(), nx, tol);
+    if (good >= k) break;
+    nc = good;
+    refresh_next = true;
+    Wbase = h->wbuf[0];
+    if ((rc = residual_step(nc, true))) return rc;
+    if ((rc = finish_w(nc, nc))) return h->fail(rc, "preconditioner callback failed");
+  }
+  if (status != LOBPCG_OK) {
+    // outputs still hold the current iterate with explicit backward errors
+    if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
+    if ((rc = residual_step(0, false))) return rc;
+  }
+  // ---- outputs
+  if ((rc = sign_normalise(h->st, n, (int)k, h->X, ld, nullptr))) return rc;
+  const cudaMemcpyKind kind =
+      mem_out == LOBPCG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  LOB_CUDA_OK(cudaMemcpy2DAsync(Xout, ldx * sizeof(double), h->X, ld * sizeof(double),
+                                k * sizeof(double), n, kind, h->st));
+  LOB_CUDA_OK(cudaMemcpyAsync(lambda, h->theta, k * sizeof(double), kind, h->st));
+  if (resnorm) LOB_CUDA_OK(cudaMemcpyAsync(resnorm, h->be, k * sizeof(double), kind, h->st));
+  if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
+  LOB_CUDA_OK(cudaStreamSynchronize(h->st));
+  h->timer.flush();
+  double mx = 0.0;
+  for (int64_t i = 0; i < k; ++i) mx = std::max(mx, be_h[i]);
+  h->stats.max_backward_error = mx;
+  h->stats.iterations = it;
+  h->stats.converged = nc;
+  h->stats.gpu_launches = g_launches - launches0;
+  h->stats.ms_spmm = h->timer.total[PH_SPMM];
+  h->stats.ms_gram = h->timer.total[PH_GRAM];
+  h->stats.ms_update = h->timer.total[PH_UPDATE];
+  h->stats.ms_residual = h->timer.total[PH_RESID];
+  h->stats.ms_small_dense = h->timer.total[PH_DENSE];
+  h->stats.ms_ortho = h->timer.total[PH_ORTHO];
+  h->stats.ms_total =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (iters) *iters = it;
+  if (status == LOBPCG_ERR_NOT_CONVERGED) return h->fail(status, "maxit reached");
+  if (status == LOBPCG_ERR_TIMEOUT) return h->fail(status, "wall-clock limit reached");
+  return LOBPCG_OK;
+}
+
+__global__ void csr_diag_kernel(int64_t n, const int32_t* rp, const int32_t* ci, const double* v,
+                                double* d) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double x = 0.0;
+  for (int p = rp[r]; p < rp[r + 1]; ++p)
+    if (ci[p] == r) x += v[p];
+  d[r] = x;
+}
+
+int copy_in(lobpcg_ctx* h, void** dst, const void* src, size_t bytes, int mem) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  LOB_CUDA_OK(cudaMemcpyAsync(*dst, src, bytes,
+                              mem == LOBPCG_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                              h->st));
+  return LOBPCG_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+LOBPCG_EXPORT int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, void* stream) {
+  if (!out) return LOBPCG_ERR_ARG;
+  *out = nullptr;
+  auto* h = new (std::nothrow) lobpcg_ctx();
+  if (!h) return LOBPCG_ERR_OOM;
+  if (opts) h->opt = *opts;
+  if (h->opt.gemm_mode != LOBPCG_GEMM_F64 && h->opt.gemm_mode != LOBPCG_GEMM_OZAKI) {
+    delete h;
+    return LOBPCG_ERR_ARG;
+  }
+  if (h->opt.ozaki_slices != 0 && (h->opt.ozaki_slices < 3 || h->opt.ozaki_slices > 7)) {
+    delete h;
+    return LOBPCG_ERR_ARG;
+  }
+  cudaGetDevice(&h->device);
+  h->st = (cudaStream_t)stream;
+  if (cudaMallocHost(&h->hbuf, 1 << 20) != cudaSuccess) {
+    delete h;
+    return LOBPCG_ERR_OOM;
+  }
+  *out = h;
+  return LOBPCG_OK;
+}
+
+LOBPCG_EXPORT void lobpcg_destroy(lobpcg_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+LOBPCG_EXPORT const char* lobpcg_last_error(lobpcg_t h) { return h ? h->err.c_str() : "null handle"; }
+
+LOBPCG_EXPORT int lobpcg_get_stats(lobpcg_t h, lobpcg_stats_t* out) {
+  if (!h || !out) return LOBPCG_ERR_ARG;
+  *out = h->stats;
+  return LOBPCG_OK;
+}
+
+LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
+                                      const int32_t* A_col, const double* A_val, int64_t A_nnz,
+                                      const int32_t* B_rowptr, const int32_t* B_col,
+                                      const double* B_val, int64_t B_nnz, const double* B_diag,
+                                      int mem) {
+  if (!h) return LOBPCG_ERR_ARG;
+  if (n <= 0 || n > (int64_t)1 << 31) return h->fail(LOBPCG_ERR_ARG, "n out of range");
+  if (!A_rowptr || !A_col || !A_val || A_nnz < 0 || A_nnz >= ((int64_t)1 << 31))
+    return h->fail(LOBPCG_ERR_ARG, "bad A");
+  if (B_rowptr && (!B_col || !B_val || B_nnz < 0 || B_nnz >= ((int64_t)1 << 31)))
+    return h->fail(LOBPCG_ERR_ARG, "bad B");
+  if (B_rowptr && B_diag) return h->fail(LOBPCG_ERR_ARG, "give B as CSR or diagonal, not both");
+  if (mem == LOBPCG_MEM_HOST) {
+    if (A_rowptr[0] != 0 || A_rowptr[n] != A_nnz) return h->fail(LOBPCG_ERR_ARG, "bad A rowptr");
+    for (int64_t i = 0; i < n; ++i)
+      if (A_rowptr[i + 1] < A_rowptr[i]) return h->fail(LOBPCG_ERR_ARG, "A rowptr not monotone");
+    for (int64_t p = 0; p < A_nnz; ++p)
+      if (A_col[p] < 0 || A_col[p] >= n) return h->fail(LOBPCG_ERR_ARG, "A column out of range");
+  }
+  h->free_ws();
+  h->release_op();
+  h->n = n;
+  h->A_nnz = A_nnz;
+  int rc;
+  if ((rc = copy_in(h, (void**)&h->A_rp, A_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
+      (rc = copy_in(h, (void**)&h->A_ci, A_col, A_nnz * sizeof(int32_t), mem)) ||
+      (rc = copy_in(h, (void**)&h->A_v, A_val, A_nnz * sizeof(double), mem)))
+    return h->fail(rc, "copying A failed");
+  h->b_kind = 0;
+  h->b_cond = 1.0;
+  if (B_rowptr) {
+    h->b_kind = 2;
+    h->B_nnz = B_nnz;
+    if ((rc = copy_in(h, (void**)&h->B_rp, B_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
+        (rc = copy_in(h, (void**)&h->B_ci, B_col, B_nnz * sizeof(int32_t), mem)) ||
+        (rc = copy_in(h, (void**)&h->B_v, B_val, B_nnz * sizeof(double), mem)))
+      return h->fail(rc, "copying B failed");
+  } else if (B_diag) {
+    h->b_kind = 1;
+    if ((rc = copy_in(h, (void**)&h->b_diag, B_diag, n * sizeof(double), mem)))
+      return h->fail(rc, "copying B failed");
+    std::vector<double> b(n);
+    if (cudaMemcpyAsync(b.data(), h->b_diag, n * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess)
+      return h->fail(LOBPCG_ERR_CUDA, "reading B failed");
+    double lo = INFINITY, hi = 0.0;
+    for (double x : b) {
+      lo = std::min(lo, std::fabs(x));
+      hi = std::max(hi, std::fabs(x));
+      if (!(x > 0)) return h->fail(LOBPCG_ERR_ARG, "diagonal B must be positive");
+    }
+    h->b_cond = hi / lo;
+  }
+  if (cudaMalloc(&h->adiag, n * sizeof(double)) != cudaSuccess)
+    return h->fail(LOBPCG_ERR_OOM, "allocation failed");
+  csr_diag_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, h->st>>>(n, h->A_rp, h->A_ci, h->A_v,
+                                                                 h->adiag);
+  ++g_launches;
+  std::vector<double> d(n);
+  if (cudaMemcpyAsync(d.data(), h->adiag, n * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return h->fail(LOBPCG_ERR_CUDA, "reading diag(A) failed");
+  h->k_kind = 0;
+  for (double x : d)
+    if (x == 0.0) {
+      h->k_kind = 2;  // Jacobi undefined: fall back to K = I and report it
+      h->err = "diag(A) has a zero entry: preconditioner set to K = I";
+      break;
+    }
+  return LOBPCG_OK;
+}
+
+LOBPCG_EXPORT int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int mem) {
+  if (!h) return LOBPCG_ERR_ARG;
+  if (h->n <= 0) return h->fail(LOBPCG_ERR_ARG, "set the operator first");
+  if (mem < 0) {
+    h->k_kind = 2;
+    return LOBPCG_OK;
+  }
+  if (!kdiag) {
+    h->k_kind = 0;
+    return LOBPCG_OK;
+  }
+  int rc = copy_in(h, (void**)&h->kdiag, kdiag, h->n * sizeof(double), mem);
+  if (rc) return h->fail(rc, "copying K failed");
+  h->k_kind = 1;
+  return LOBPCG_OK;
+}
+
+LOBPCG_EXPORT int lobpcg_set_precond_callback(lobpcg_t h, lobpcg_precond_fn fn, void* ctx) {
+  if (!h || !fn) return LOBPCG_ERR_ARG;
+  h->cb = fn;
+  h->cb_ctx = ctx;
+  h->k_kind = 3;
+  return LOBPCG_OK;
+}
+
+LOBPCG_EXPORT int lobpcg_solve(lobpcg_t h, int64_t k, double tol, const double* X0,
+                               int64_t ldx0, uint64_t seed, int mem_in, double* lambda,
+                               double* X, int64_t ldx, int mem_out, int64_t* iters,
+                               double* resnorm) {
+  if (!h) return LOBPCG_ERR_ARG;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return h->fail(LOBPCG_ERR_ARG, "handle belongs to another device");
+  h->err.clear();
+  int rc = solve_impl(h, k, tol, X0, ldx0, seed, mem_in, lambda, X, ldx, mem_out, iters, resnorm);
+  if (rc == LOBPCG_ERR_CUDA && h->err.empty()) {
+    cudaError_t e = cudaGetLastError();
+    h->err = std::string("CUDA error: ") + cudaGetErrorString(e);
+  } else if (rc && h->err.empty()) {
+    h->err = "solve failed";
+  }
+  return rc;
+}

@@ -1,0 +1,204 @@
+"""End-to-end parity of the CUDA solver (through the C ABI) with the oracle,
+closed forms and brute force, plus the error paths."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import dense
+from oracle import lobpcg as L
+import paper_1704_07458_gb300 as gb
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["f64"]
+
+
+def _oracle(p, seed=0, nx=None, opts=None):
+    A = p.A
+    pen = L.Pencil(A.n, (A.rowptr, A.col, A.val), p.b_diag, p.kdiag)
+    nx = nx or synth.block_width(p.k, A.n)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, A.n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, A.n, 16).T
+    return pen, L.lobpcg(pen, X0, p.k, p.tol, Om, opts)
+
+
+def _gpu(p, seed=0, X0=None, mode="f64", device=False, **opts):
+    torch_cuda()
+    s = gb.Solver(gemm_mode=mode, **opts)
+    s.set_operator(p.A.rowptr, p.A.col, p.A.val, b_diag=p.b_diag)
+    if p.kdiag is None:
+        s.set_precond_identity()
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, seed=seed, device=device)
+    st = s.stats()
+    s.close()
+    return lam, X, it, be, rc, st
+
+
+def _check_pairs(p, lam, X, be, normA, normB, tol_orth=1e-12):
+    """Properties that hold at any size: B-orthonormality, explicit Eq. (9)."""
+    A = sp.csr_matrix((p.A.val, p.A.col, p.A.rowptr), shape=(p.n, p.n))
+    BX = X if p.b_diag is None else p.b_diag[:, None] * X
+    np.testing.assert_allclose(X.T @ BX, np.eye(p.k), atol=tol_orth)
+    R = A @ X - BX * lam[None, :]
+    ref = L.backward_error(R, X, lam, normA, normB)
+    assert np.all(ref <= p.tol * (1 + 1e-6)), ref.max()
+    np.testing.assert_allclose(be, ref, rtol=1e-6, atol=1e-14)
+    assert np.all(np.diff(lam) >= -1e-14)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_c1_closed_form_and_oracle(mode):
+    p = synth.make_problem("lap2d_32")
+    nx = synth.block_width(p.k)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, nx)
+    lam, X, it, be, rc, st = _gpu(p, X0=X0, mode=mode)
+    assert rc == 0
+    np.testing.assert_allclose(lam, p.closed_form[:8], rtol=1e-10)
+    _, r = _oracle(p)
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    np.testing.assert_allclose(st["norm_a"], r.normA, rtol=1e-12)
+    _check_pairs(p, lam, X, be, r.normA, r.normB)
+    # non-degenerate pairs: the sign-normalised vectors agree with the oracle
+    for i in [0, 3]:
+        np.testing.assert_allclose(X[:, i], r.X[:, i], atol=1e-7)
+    assert abs(it - r.iters) <= max(3, r.iters // 10)
+
+
+def test_c1_device_buffers_and_seeded_start():
+    torch = torch_cuda()
+    p = synth.make_problem("lap2d_32")
+    s = gb.Solver()
+    rp, ci = torch.from_numpy(p.A.rowptr).cuda(), torch.from_numpy(p.A.col).cuda()
+    s.set_operator(rp, ci, torch.from_numpy(p.A.val).cuda())
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=None, seed=0, device=True)
+    torch.cuda.synchronize()
+    assert rc == 0 and X.is_cuda
+    np.testing.assert_allclose(lam.cpu().numpy(), p.closed_form[:8], rtol=1e-10)
+    s.close()
+
+
+def test_generalised_brute_force():
+    n_side = 12
+    b = synth.uniform_block(3, synth.STREAM_BDIAG, n_side ** 2, 1.0, 2.0)
+    A = synth.add_diagonal(synth.laplacian_2d_dirichlet(n_side),
+                           synth.uniform_block(3, synth.STREAM_POTENTIAL, n_side ** 2))
+    p = synth.Problem("bf", A, 10, 1e-10, b_diag=b, kdiag=A.diagonal())
+    lam, X, it, be, rc, st = _gpu(p, seed=3)
+    assert rc == 0
+    w, _ = dense.pencil_eigh(A.to_dense(), np.diag(b))
+    np.testing.assert_allclose(lam, w[:10], rtol=1e-10)
+    _check_pairs(p, lam, X, be, st["norm_a"], st["norm_b"])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_c2_reduced_oracle_parity(mode):
+    p = synth.make_problem("lap3d_64_diagB", N=16, k=16)
+    lam, X, it, be, rc, st = _gpu(p, mode=mode)
+    assert rc == 0
+    _, r = _oracle(p)
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    _check_pairs(p, lam, X, be, r.normA, r.normB)
+
+
+def test_forced_orthogonalisation_path():
+    p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
+    lam, X, it, be, rc, st = _gpu(p, tau_skip=1.0)
+    assert rc == 0 and st["flip_iteration"] == 1 and st["ortho_calls"] >= it
+    _, r = _oracle(p, opts=L.Options(tau_skip=1.0))
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    _check_pairs(p, lam, X, be, r.normA, r.normB)
+
+
+def test_periodic_singular_hamiltonian():
+    N = 6
+    A = synth.hamiltonian_3d_periodic(N, np.zeros(N ** 3))
+    p = synth.Problem("h0", A, 7, 1e-8, kdiag=None)
+    lam, X, it, be, rc, st = _gpu(p)
+    assert rc == 0 and abs(lam[0]) < 1e-12
+    j = np.arange(N)
+    one = 2.0 * np.sin(np.pi * j / N) ** 2
+    ref = np.sort((one[:, None, None] + one[None, :, None] + one[None, None, :]).ravel())
+    np.testing.assert_allclose(lam, ref[:7], atol=1e-10)
+
+
+def test_explicit_products_and_certification_off():
+    p = synth.make_problem("lap2d_32")
+    lam, X, it, be, rc, st = _gpu(p, implicit="never", certify=1)
+    assert rc == 0
+    np.testing.assert_allclose(lam, p.closed_form[:8], rtol=1e-10)
+
+
+def test_breakdown_not_converged_and_bad_args():
+    p = synth.make_problem("lap2d_32")
+    X0 = synth.normal_block(0, 1, p.n, 10)
+    X0[:, 7] = X0[:, 2]
+    lam, X, it, be, rc, st = _gpu(p, X0=X0)
+    assert rc == gb.LOBPCG_ERR_BREAKDOWN
+    lam, X, it, be, rc, st = _gpu(p, maxit=3)
+    assert rc == gb.LOBPCG_ERR_NOT_CONVERGED and it == 3
+    s = gb.Solver()
+    s.set_operator(p.A.rowptr, p.A.col, p.A.val)
+    with pytest.raises(gb.LobpcgError):
+        s.solve(0, 1e-8)
+    with pytest.raises(gb.LobpcgError):
+        s.solve(5, -1.0)
+    s.close()
+
+
+class _DevView:
+    """Zero-copy view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, addr, rows, cols, ld):
+        self.__cuda_array_interface__ = {
+            "shape": (rows, cols), "typestr": "<f8", "data": (addr, False),
+            "strides": (ld * 8, 8), "version": 2}
+
+
+def test_callback_preconditioner_matches_jacobi():
+    torch = torch_cuda()
+    p = synth.make_problem("lap2d_32")
+    kd = torch.from_numpy(p.A.diagonal()).cuda()
+    calls = []
+
+    def jacobi(n, ncols, R, ldr, W, ldw, stream):
+        Rt = torch.as_tensor(_DevView(R, n, ncols, ldr), device="cuda")
+        Wt = torch.as_tensor(_DevView(W, n, ncols, ldw), device="cuda")
+        Wt.copy_(Rt / kd[:, None])
+        torch.cuda.synchronize()
+        calls.append(ncols)
+        return 0
+
+    s = gb.Solver()
+    s.set_operator(p.A.rowptr, p.A.col, p.A.val)
+    s.set_precond_callback(jacobi)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, 10)
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0)
+    s.close()
+    assert rc == 0 and len(calls) >= it
+    lam2, *_ = _gpu(p, X0=X0)
+    np.testing.assert_allclose(lam, lam2, rtol=1e-12)
+
+
+def test_callback_error_is_reported():
+    p = synth.make_problem("lap2d_32")
+    s = gb.Solver()
+    s.set_operator(p.A.rowptr, p.A.col, p.A.val)
+    s.set_precond_callback(lambda *a: 1)
+    lam, X, it, be, rc = s.solve(p.k, p.tol, raise_on_error=False)
+    assert rc == gb.LOBPCG_ERR_CALLBACK
+    s.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_c2_full_size_properties(mode):
+    """Bench workload (64^3 Laplacian, diagonal B, k = 64): any-size properties."""
+    p = synth.make_problem("lap3d_64_diagB")
+    lam, X, it, be, rc, st = _gpu(p, mode=mode)
+    assert rc == 0
+    _check_pairs(p, lam, X, be, st["norm_a"], st["norm_b"], tol_orth=1e-10)
+    # Ritz values are upper bounds of the exact eigenvalues; with B in [1, 2]
+    # the pencil's spectrum lies between the Laplacian's divided by 2 and by 1
+    lap = synth.problems.closed_form_laplacian((64, 64, 64), 64)
+    assert np.all(lam >= lap / 2.0 - 1e-12) and np.all(lam <= lap + 1e-12)

@@ -34,7 +34,7 @@ def _run(p, seed=0, opts=None, scaleA=1.0, scaleB=None, nx=None):
     pen = _pencil(A, b, kd)
     nx = nx or synth.block_width(p.k, A.n)
     X0 = synth.normal_block(seed, synth.STREAM_X0, A.n, nx)
-    Om = synth.normal_block(seed, synth.STREAM_OMEGA, 16, A.n)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, A.n, 16).T
     return pen, L.lobpcg(pen, X0, p.k, p.tol, Om, opts)
 
 
@@ -217,7 +217,7 @@ def test_cp_reduces_to_lq_form_without_locking():
 def test_norm_estimate_bounds():
     A = synth.laplacian_2d_dirichlet(20)
     pen = _pencil(A)
-    Om = synth.normal_block(0, synth.STREAM_OMEGA, 16, A.n)
+    Om = synth.normal_block(0, synth.STREAM_OMEGA, A.n, 16).T
     est = L.norm_estimate(pen.A_mul, Om)
     true = np.linalg.norm(A.to_dense(), 2)
     assert 0.3 * true < est <= true
@@ -348,7 +348,7 @@ def test_breakdown_and_not_converged():
     pen = _pencil(A)
     X0 = synth.normal_block(0, 1, A.n, 4)
     X0[:, 3] = X0[:, 1]
-    Om = synth.normal_block(0, 5, 16, A.n)
+    Om = synth.normal_block(0, 5, A.n, 16).T
     assert L.lobpcg(pen, X0, 2, 1e-8, Om).status == L.BREAKDOWN
     X0 = synth.normal_block(0, 1, A.n, 4)
     r = L.lobpcg(pen, X0, 2, 1e-8, Om, L.Options(maxit=3))
