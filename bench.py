@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark: time to the k smallest eigenpairs at backward-stable tol 1e-8.
+
+Workload (default): generalised pencil from a 3D 7-point Dirichlet Laplacian on
+a 64^3 grid (n = 262,144, nnz = 1,810,432), diagonal B with entries U[1, 2]
+from the seed, Jacobi preconditioner, k = 64 (block width 71), tol 1e-8 in
+the backward-stable criterion of Eq. (9), synthetic seeded inputs.
+
+One step = one complete solve through the C ABI (norm estimates, initial
+Rayleigh-Ritz, all iterations of Algorithm 8, exit certification).
+  value  device-resident inputs (operator already in HBM), CUDA events on the
+         solver's stream around K solves; seconds per solve, lower is better.
+  e2e    the same through the C ABI with host buffers: the operator and X0 are
+         copied from pinned host memory and the eigenpairs read back, per step.
+The working set (15 blocks of 262,144 x 72 doubles, 151 MB each) is larger than
+the 129 MB L2, so no L2 flush is inserted between steps.
+
+--impl reference times the CPU oracle (plain FP64 numpy) on a bounded sample
+of the same workload and extrapolates to a full solve.
+Under torchrun (N > 1) every rank solves its own replica (seed = rank); there
+is no collective on the data path ("replicas only").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-k-eigenpairs at backward-stable tol 1e-8; SpMM HBM GB/s; Gram TFLOP/s"
+WORKLOAD = "lap3d_64_diagB"
+# Iterations the CPU oracle needs to converge on this workload with seed 0
+# (measured by running oracle.lobpcg to convergence on the same inputs); used
+# to extrapolate the bounded oracle samples to a full solve.
+ORACLE_ITERS = {"lap3d_64_diagB": 726}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores and DMMA), nominal
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        rows = [l.split(",") for l in open(self.file.name) if l.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(p, seed, iters):
+    """Run the CPU oracle for `iters` iterations; return (seconds, seconds/iteration)."""
+    import numpy as np
+    import synth
+    from oracle import lobpcg as L
+    nx = synth.block_width(p.k)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, p.n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, p.n, 16).T
+    pen = L.Pencil(p.n, (p.A.rowptr, p.A.col, p.A.val), p.b_diag, p.kdiag)
+    t0 = time.perf_counter()
+    L.lobpcg(pen, X0, p.k, p.tol, Om, L.Options(maxit=iters, certify=False))
+    dt = time.perf_counter() - t0
+    return dt, dt / iters
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    p = synth.make_problem(args.workload, seed=0)
+    sample_iters = args.ref_iters
+    full = ORACLE_ITERS.get(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(p, 0, 1)
+    vals = []
+    for _ in range(args.steps):
+        _, per_it = oracle_sample(p, 0, sample_iters)
+        vals.append(per_it * full)
+    v = statistics.median(vals)
+    sample = (f"{sample_iters} oracle iterations per step on the full workload, "
+              f"extrapolated to the oracle's {full} iterations to convergence")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args, p),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, p):
+    return {"workload": f"{args.workload}: {p.note}, n={p.n}, nnz={p.A.nnz}, k={p.k}, "
+                        f"tol={p.tol}", "n": p.n, "nnz": p.A.nnz, "k": p.k, "tol": p.tol,
+            "block_width": None, "gemm_mode": args.mode,
+            "l2": "working set > L2 (15 blocks of n x 72 doubles, 151 MB each); no flush",
+            "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "1gpu"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="f64", choices=["f64", "ozaki"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--ref-iters", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import synth
+    import paper_1704_07458_gb300 as gb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    peaks = load_peaks()
+    seed = rank
+    p = synth.make_problem(args.workload, seed=seed)
+    stream = torch.cuda.current_stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    A_rp, A_ci, A_v = dev(p.A.rowptr), dev(p.A.col), dev(p.A.val)
+    bd = dev(p.b_diag) if p.b_diag is not None else None
+
+    solver = gb.Solver(stream=stream, gemm_mode=args.mode)
+    solver.set_operator(A_rp, A_ci, A_v, b_diag=bd)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        lam, X, it, be, rc = solver.solve(p.k, p.tol, seed=seed, device=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = {}
+    e0.record(stream)
+    for _ in range(args.steps):
+        lam, X, it, be, rc = solver.solve(p.k, p.tol, seed=seed, device=True)
+        st = solver.stats()
+        for key, v in st.items():
+            tot[key] = tot.get(key, 0) + v
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    assert rc == gb.LOBPCG_OK, f"solve failed: {rc}"
+    bemax = float(be.max().item())
+
+    # ---- end to end through the C ABI with host buffers
+    nx = synth.block_width(p.k)
+    X0h = torch.from_numpy(synth.normal_block(seed, synth.STREAM_X0, p.n, nx)).pin_memory()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_ci, h_v = pin(p.A.rowptr), pin(p.A.col), pin(p.A.val)
+    h_b = pin(p.b_diag) if p.b_diag is not None else None
+    lam_h = torch.empty(p.k, dtype=torch.float64).pin_memory()
+    X_h = torch.empty((p.n, p.k), dtype=torch.float64).pin_memory()
+    be_h = torch.empty(p.k, dtype=torch.float64).pin_memory()
+    h2d = (h_rp.numel() * 4 + h_ci.numel() * 4 + h_v.numel() * 8 +
+           (h_b.numel() * 8 if h_b is not None else 0) + X0h.numel() * 8)
+    d2h = (lam_h.numel() + X_h.numel() + be_h.numel()) * 8
+    e2e_solver = gb.Solver(stream=stream, gemm_mode=args.mode)
+    e2e_steps = max(1, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc_e = gb.lobpcg_set_operator(e2e_solver.h, p.n, h_rp, h_ci, h_v, p.A.nnz, B_diag=h_b,
+                                      mem=gb.LOBPCG_MEM_HOST)
+        assert rc_e == 0
+        rc_e, _ = gb.lobpcg_solve(e2e_solver.h, p.k, p.tol, X0h, nx, seed, gb.LOBPCG_MEM_HOST,
+                                  lam_h, X_h, p.k, gb.LOBPCG_MEM_HOST, be_h)
+        assert rc_e == 0, rc_e
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- roofline of the dominant n-scaled kernel over the timed region
+    phases = {
+        "spmm": (tot["ms_spmm"], tot["spmm_bytes"], "hbm"),
+        "gram": (tot["ms_gram"], tot["gram_flops"], "alu" if args.mode == "f64" else "tensor"),
+        "update": (tot["ms_update"], tot["update_flops"],
+                   "alu" if args.mode == "f64" else "tensor"),
+    }
+    dom = max(phases, key=lambda k: phases[k][0])
+    t_ms, work, bound = phases[dom]
+    if bound == "hbm":
+        achieved = work / (t_ms * 1e-3) / 1e9
+        peak, unit = peaks["hbm_gbs"], "GB/s"
+        peak_src = "measured hbm_gbs"
+    elif bound == "alu":
+        achieved = work / (t_ms * 1e-3) / 1e12
+        peak, unit = FP64_NOMINAL_TFLOPS, "TFLOP/s"
+        peak_src = "nominal GB300 FP64 rate (no measured FP64 peak)"
+    else:
+        achieved = work / (t_ms * 1e-3) / 1e12
+        peak, unit = peaks["bf16_tflops_sustained"], "TFLOP/s"
+        peak_src = "measured bf16_tflops_sustained"
+    per_phase = {k: {"ms_per_solve": v[0] / args.steps,
+                     "rate": (v[1] / (v[0] * 1e-3) / (1e9 if v[2] == "hbm" else 1e12))
+                     if v[0] > 0 else None,
+                     "unit": "GB/s" if v[2] == "hbm" else "TFLOP/s (FP64-equivalent)"}
+                 for k, v in phases.items()}
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_src, "phases": per_phase}
+
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(args, p),
+        "iterations": int(it), "max_backward_error": bemax,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(tot["gpu_launches"]),
+        "clocks": clk, "roofline": roofline,
+        "small_dense_ms_per_solve": tot["ms_small_dense"] / args.steps,
+        "residual_ms_per_solve": tot["ms_residual"] / args.steps,
+    }
+    line["config"]["block_width"] = int(st["n_x"])
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample_iters = args.ref_iters
+        dt, per_it = oracle_sample(p, seed, sample_iters)
+        line["cpu_baseline"] = {
+            "value": per_it * it, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{sample_iters} oracle iterations ({dt:.1f} s) on the full workload, "
+                      f"extrapolated per iteration to this run's {it} iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    e2e_solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,12 @@ class lobpcg_stats_t(ctypes.Structure):
         ("ms_small_dense", ctypes.c_double),
         ("ms_ortho", ctypes.c_double),
         ("ms_total", ctypes.c_double),
+        ("spmm_calls", ctypes.c_int64),
+        ("gram_calls", ctypes.c_int64),
+        ("update_calls", ctypes.c_int64),
+        ("spmm_bytes", ctypes.c_double),
+        ("gram_flops", ctypes.c_double),
+        ("update_flops", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -396,6 +396,30 @@ int sign_normalise(cudaStream_t st, int64_t n, int m, double* X, int64_t ldx, vo
   return LOBPCG_OK;
 }
 
+// ------------------------------------------------------ balance exponents
+// out[k] = floor(log2(G_kk) / 2), i.e. 2^out[k] is within a factor 2 of the
+// column norm sqrt(G_kk) (0 for a non-positive diagonal).  Integer ops only.
+__global__ void diag_exponents_kernel(int n, const double* __restrict__ G, int64_t ldg,
+                                      int* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const long long b = __double_as_longlong(G[k + (int64_t)k * ldg]);
+  const int be = (int)((b >> 52) & 0x7FF);
+  int e = 0;
+  if (b > 0 && be > 0 && be < 0x7FF) {
+    const int u = be - 1023;
+    e = (u >= 0) ? u / 2 : -((-u + 1) / 2);
+  }
+  out[k] = e;
+}
+
+int diag_exponents(cudaStream_t st, int n, const double* G, int64_t ldg, int* out) {
+  if (n <= 0) return LOBPCG_OK;
+  diag_exponents_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, G, ldg, out);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
 // ------------------------------------------------------------- Philox4x32-10
 // Salmon et al. (SC'11): ten rounds of two 32x32->64 multiplications with the
 // constants 0xD2511F53 / 0xCD9E8D57 and a Weyl key schedule 0x9E3779B9 /

@@ -23,9 +23,13 @@ int gram_ozaki(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, d
 // Y = beta * Y0 + alpha * S C; S segments (n x s), C s x m column-major.
 int update_f64(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc,
                int m, double alpha, double beta, const SegList& Y0, const OutList& Y);
+// colexp (device, s ints, may be nullptr): column k of S is scaled by 2^-colexp[k]
+// and row k of C by 2^colexp[k] (exact), so that column scalings of S that C
+// undoes (e.g. the D of Rayleigh-Ritz) do not cost fixed-point precision.
+// nullptr: the exponents are taken from a column pass over S.
 int update_ozaki(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc,
                  int m, double alpha, double beta, const SegList& Y0, const OutList& Y,
-                 int slices, void* work, int64_t work_bytes);
+                 int slices, void* work, int64_t work_bytes, const int* colexp = nullptr);
 int64_t update_ozaki_workspace(int64_t n, int s, int m, int slices);
 
 // Residual / preconditioner / Eq. (9) norms for columns c0..m-1.
@@ -39,6 +43,9 @@ int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, cons
 int64_t colsumsq_workspace(int64_t n, int m);
 int colsumsq(cudaStream_t st, int64_t n, const double* Y, int64_t ld, int m, double* out,
              void* partial);
+
+// out[k] = floor(log2(G_kk)/2) for a Gram G (column-major, leading dim ldg).
+int diag_exponents(cudaStream_t st, int n, const double* G, int64_t ldg, int* out);
 
 // Y = diag(b) X (n x m).
 int diag_scale(cudaStream_t st, int64_t n, int m, const double* b, const double* X,

@@ -105,6 +105,7 @@ struct lobpcg_ctx {
   double *X, *P, *AX, *AP, *AW, *BX, *BP, *BW, *Xn, *Pn, *AXn, *APn, *BXn, *BPn, *Om;
   double* wbuf[4];
   double *theta, *be, *colA, *colB, *Gw, *Gs, *SAS, *SBS, *Cm, *PAP, *PAPn;
+  int *cexp, *zexp;  // column balance exponents of S, and all zeros
   void* gwork = nullptr;
   int64_t gwork_bytes = 0;
   void* uwork = nullptr;
@@ -185,6 +186,9 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   for (double** b : vecs)
     if ((rc = dalloc(h, (void**)b, (size_t)std::max<int64_t>(nsmax, s) * 2 * sizeof(double))))
       return rc;
+  if ((rc = dalloc(h, (void**)&h->cexp, (size_t)nsmax * sizeof(int)))) return rc;
+  if ((rc = dalloc(h, (void**)&h->zexp, (size_t)nsmax * sizeof(int)))) return rc;
+  LOB_CUDA_OK(cudaMemsetAsync(h->zexp, 0, (size_t)nsmax * sizeof(int), h->st));
   // Gram scratch: the widest use is S^T [AW, BW] (3 nx x 2 nx) or X^T [AX, BX].
   const int mode = gemm_mode(h), sl = slices(h);
   // The slab count depends on the shape, so take the maximum over every Gram
@@ -213,16 +217,22 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
 // ---- thin wrappers choosing the arithmetic of the dense contractions
 
 int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t ldg) {
+  h->stats.gram_calls++;
+  h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
   if (gemm_mode(h))
     return gram_ozaki(h->st, h->n, U, V, G, ldg, slices(h), h->gwork, h->gwork_bytes);
   return gram_f64(h->st, h->n, U, V, G, ldg, h->gwork, h->gwork_bytes);
 }
 
+// colexp: per-column power-of-two balance of S for the tensor-core path (see
+// update_ozaki); h->zexp when the columns of S are already balanced.
 int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m, double alpha,
-           double beta, const SegList& Y0, const OutList& Y) {
+           double beta, const SegList& Y0, const OutList& Y, const int* colexp) {
+  h->stats.update_calls++;
+  h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
   if (gemm_mode(h))
     return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y, slices(h), h->uwork,
-                        h->uwork_bytes);
+                        h->uwork_bytes, colexp);
   return update_f64(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y);
 }
 
@@ -232,6 +242,10 @@ OutList out1(double* p, int64_t ld, int m) { return OutList{{p, p}, {ld, ld}, m}
 int apply_AB(lobpcg_ctx* h, const double* X, int m, double* AY, double* BY) {
   if (m <= 0) return LOBPCG_OK;
   Scoped sc(h->timer, PH_SPMM);
+  const double n = (double)h->n;
+  h->stats.spmm_calls++;
+  h->stats.spmm_bytes += h->A_nnz * 12.0 + 4.0 * (n + 1) + 16.0 * n * m +
+                         ((BY && h->b_kind == 1) ? 8.0 * n + 16.0 * n * m : 0.0);
   int rc = spmm(h->st, h->n, h->A_rp, h->A_ci, h->A_v, X, h->ld, m, AY, h->ld,
                 (BY && h->b_kind == 1) ? h->b_diag : nullptr, BY, h->ld);
   if (rc || !BY) return rc;
@@ -308,7 +322,8 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
     // U = U - V (V^T B U), with V^T B U formed as (BV)^T U
     if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv))) return rc;
     double* dst = spare(Ubase, nullptr);
-    if ((rc = update(h, V, h->Gs, nv, nu, -1.0, 1.0, seg1(U, h->ld, nu), out1(dst, h->ld, nu))))
+    if ((rc = update(h, V, h->Gs, nv, nu, -1.0, 1.0, seg1(U, h->ld, nu), out1(dst, h->ld, nu),
+                     h->zexp)))
       return rc;
     U = Ubase = dst;
     for (int j = 0; j < 3; ++j) {
@@ -318,6 +333,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
         BUp = BU;
       }
       if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu))) return rc;
+      if ((rc = diag_exponents(h->st, nu, h->Gs, nu, h->cexp))) return rc;
       int keep = 0;
       {
         Scoped sd(h->timer, PH_DENSE);
@@ -330,7 +346,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
       }
       dst = spare(Ubase, nullptr);
       if ((rc = update(h, seg1(U, h->ld, nu), h->Cm, nu, keep, 1.0, 0.0, seg_empty(),
-                       out1(dst, h->ld, keep))))
+                       out1(dst, h->ld, keep), h->cexp)))
         return rc;
       U = Ubase = dst;
       nu = keep;
@@ -431,6 +447,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
     seg_push(V, BXp, ld, (int)nx);
     if ((rc = gram(h, seg1(h->X, ld, (int)nx), V, h->Gw, nx))) return rc;
   }
+  if ((rc = diag_exponents(h->st, (int)nx, h->Gw + nx * nx, (int)nx, h->cexp))) return rc;
   bool breakdown = false;
   {
     Scoped sc(h->timer, PH_DENSE);
@@ -441,7 +458,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   {
     Scoped sc(h->timer, PH_UPDATE);
     if ((rc = update(h, seg1(h->X, ld, (int)nx), h->Cm, nx, (int)nx, 1.0, 0.0, seg_empty(),
-                     out1(h->Xn, ld, (int)nx))))
+                     out1(h->Xn, ld, (int)nx), h->cexp)))
       return rc;
   }
   std::swap(h->X, h->Xn);
@@ -549,6 +566,11 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       // Algorithm 8, line 16 and Sec. 5.2: [X, P] = S [C_x, C_p] (+ implicit products)
       const int mo = (int)nx + npn;
       const bool refresh = refresh_next || (it % refresh_every == 0);
+      const int* bal = h->zexp;
+      if (!use_ortho) {
+        if ((rc = diag_exponents(h->st, ns, h->SBS, ns, h->cexp))) return rc;
+        bal = h->cexp;
+      }
       {
         Scoped sc(h->timer, PH_UPDATE);
         SegList S = seg_empty();
@@ -556,21 +578,21 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
         seg_push(S, h->P, ld, np);
         seg_push(S, Wp, ld, nw);
         OutList O{{h->Xn, h->Pn}, {ld, ld}, (int)nx};
-        if ((rc = update(h, S, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), O))) return rc;
+        if ((rc = update(h, S, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), O, bal))) return rc;
         if (implicit && !refresh) {
           SegList AS = seg_empty();
           seg_push(AS, h->AX, ld, (int)nx);
           seg_push(AS, h->AP, ld, np);
           seg_push(AS, h->AW, ld, nw);
           OutList AO{{h->AXn, h->APn}, {ld, ld}, (int)nx};
-          if ((rc = update(h, AS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), AO))) return rc;
+          if ((rc = update(h, AS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), AO, bal))) return rc;
           if (h->b_kind == 2) {
             SegList BS = seg_empty();
             seg_push(BS, h->BX, ld, (int)nx);
             seg_push(BS, h->BP, ld, np);
             seg_push(BS, h->BW, ld, nw);
             OutList BO{{h->BXn, h->BPn}, {ld, ld}, (int)nx};
-            if ((rc = update(h, BS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), BO))) return rc;
+            if ((rc = update(h, BS, h->Cm, ns, mo, 1.0, 0.0, seg_empty(), BO, bal))) return rc;
           }
         }
       }

@@ -14,7 +14,16 @@ from gpu_util import torch_cuda, dev, host, dev_i32, gamma
 
 pytestmark = pytest.mark.gpu
 
-MODES = [(gb.LOBPCG_GEMM_F64, 0)]
+MODES = [(gb.LOBPCG_GEMM_F64, 0), (gb.LOBPCG_GEMM_OZAKI, 6), (gb.LOBPCG_GEMM_OZAKI, 4),
+         (gb.LOBPCG_GEMM_OZAKI, 7)]
+
+
+def ozaki_unit(slices):
+    """Per-term error unit of the S-slice split: truncation of the fixed-point
+    digits (2^(1-8S) of the chunk maximum, both operands) plus the dropped
+    digit pairs of levels above S + 1 (< 4 S 2^(-8S) of the product of maxima),
+    with a factor 4 of slack."""
+    return 4 * (4 + 4 * slices) * 2.0 ** (-8 * slices)
 
 
 def _csr_with_empty_rows():
@@ -85,6 +94,14 @@ def test_gram_parity(n, p, q, mode, slices):
     got = host(G).reshape(q, p + 3).T[:p, :]
     ref = ok.gram(U, V)
     bound = 2 * gamma(n) * (np.abs(U).T @ np.abs(V))
+    if mode == gb.LOBPCG_GEMM_OZAKI:
+        # per 64-row chunk c: unit * 64 * max_c|u_i| * max_c|v_j| (2x for the exponent bound)
+        nck = (n + 63) // 64
+        mu = np.zeros((nck, p)); mv = np.zeros((nck, q))
+        for c in range(nck):
+            mu[c] = np.abs(U[64 * c:64 * c + 64]).max(0)
+            mv[c] = np.abs(V[64 * c:64 * c + 64]).max(0)
+        bound = bound + ozaki_unit(slices) * 64 * 4 * (mu.T @ mv) + 2.0 ** -44 * (np.abs(U).T @ np.abs(V))
     assert np.all(np.abs(got - ref) <= bound + 1e-300)
 
 
@@ -104,6 +121,11 @@ def test_update_parity(n, s, m, beta, mode, slices):
     assert rc == 0
     ref = beta * Y0 - ok.update(S, C)
     bound = 2 * gamma(s + 1) * (np.abs(S) @ np.abs(C) + abs(beta) * np.abs(Y0))
+    if mode == gb.LOBPCG_GEMM_OZAKI:
+        # columns of S balanced by 2^E_k (E_k its exponent bound), rows of C by 2^-E_k:
+        # the balanced S has entries below 1, the balanced C entries below 2 max|S_k| |C_kj|
+        Ct = np.abs(C) * (2 * np.abs(S).max(0))[:, None]
+        bound = bound + ozaki_unit(slices) * 4 * s * Ct.max(0)[None, :] + 2.0 ** -52 * np.abs(ref)
     assert np.all(np.abs(host(Yd, m) - ref) <= bound + 1e-300)
 
 
