@@ -165,6 +165,26 @@ int lobpcg_gram(int64_t n, const double* U, int64_t ldu, int64_t p, const double
                 void* work, int64_t work_bytes, void* stream);
 int64_t lobpcg_gram_workspace(int64_t n, int64_t p, int64_t q, int mode, int slices);
 
+/* Allocation-free Gram.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory when they need a Gram (code inside a
+ * framework that owns the memory pool, callbacks run under an allocator lock,
+ * loops that must not call cudaMalloc/cudaFree because those synchronise).
+ * Computes G = U^T V exactly as lobpcg_gram with mode LOBPCG_GEMM_OZAKI (same
+ * arguments, same accuracy; the row split may differ, so results may differ
+ * from lobpcg_gram in the last bits), taking its scratch from a fixed 16 MiB
+ * array in the library's device memory that every GPU loading the library
+ * holds until the process exits.  It calls no allocator.
+ * Limits: p * q * 16 bytes must fit in that array (p * q <= 1,048,576);
+ * larger shapes return LOBPCG_ERR_ARG before any device work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls whose executions overlap on the GPU (different
+ * streams, or different host threads) race on it and must be serialised by
+ * the caller.  Nothing in it needs to start at zero. */
+int lobpcg_gram_noalloc(int64_t n, const double* U, int64_t ldu, int64_t p, const double* V,
+                        int64_t ldv, int64_t q, double* G, int64_t ldg, int slices, void* stream);
+
 /* Basis update Y = beta * Y0 + alpha * S C (Eq. 10-11): S n x s row-major, C
  * s x m column-major (leading dimension ldc), Y and Y0 n x m row-major (Y0 may
  * be NULL when beta == 0; Y must not alias S).  mode/slices as lobpcg_gram. */

@@ -29,7 +29,7 @@ EXPORTED = [
     "lobpcg_create", "lobpcg_set_operator", "lobpcg_set_precond_diag",
     "lobpcg_set_precond_callback", "lobpcg_solve", "lobpcg_get_stats", "lobpcg_last_error",
     "lobpcg_destroy", "lobpcg_spmm", "lobpcg_gram", "lobpcg_gram_workspace",
-    "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal",
+    "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
 ]
 
 
@@ -122,6 +122,7 @@ def load(build_if_missing=False):
         "lobpcg_spmm": (I32, [I64, P, P, P, P, I64, I64, P, I64, P, P, I64, P]),
         "lobpcg_gram": (I32, [I64, P, I64, I64, P, I64, I64, P, I64, I32, I32, P, I64, P]),
         "lobpcg_gram_workspace": (I64, [I64, I64, I64, I32, I32]),
+        "lobpcg_gram_noalloc": (I32, [I64, P, I64, I64, P, I64, I64, P, I64, I32, P]),
         "lobpcg_update": (I32, [I64, P, I64, I64, P, I64, I64, D, D, P, I64, P, I64, I32, I32,
                                 P]),
         "lobpcg_residual": (I32, [I64, P, P, P, I64, I64, I64, P, P, P, I64, D, D, P, P]),
@@ -227,6 +228,12 @@ def lobpcg_gram(n, U, ldu, p, V, ldv, q, G, ldg, mode=LOBPCG_GEMM_F64, slices=0,
                 work_bytes=0, stream=None):
     return load().lobpcg_gram(n, ptr(U), ldu, p, ptr(V), ldv, q, ptr(G), ldg, mode, slices,
                               ptr(work), work_bytes, stream_ptr(stream))
+
+
+def lobpcg_gram_noalloc(n, U, ldu, p, V, ldv, q, G, ldg, slices=0, stream=None):
+    """G = U^T V without allocating (fixed in-library scratch; see lobpcg.h)."""
+    return load().lobpcg_gram_noalloc(n, ptr(U), ldu, p, ptr(V), ldv, q, ptr(G), ldg, slices,
+                                      stream_ptr(stream))
 
 
 def lobpcg_update(n, S, lds, s, C, ldc, m, alpha, beta, Y0, ldy0, Y, ldy,

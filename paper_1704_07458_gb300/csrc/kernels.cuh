@@ -20,6 +20,10 @@ int64_t gram_ozaki_workspace(int64_t n, int p, int q, int slices);
 int gram_ozaki(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
                int64_t ldg, int slices, void* work, int64_t work_bytes);
 
+// As gram_ozaki, with as many row slabs as fit in work_bytes (fixed scratch).
+int gram_ozaki_bounded(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
+                       int64_t ldg, int slices, void* work, int64_t work_bytes);
+
 // Y = beta * Y0 + alpha * S C; S segments (n x s), C s x m column-major.
 int update_f64(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc,
                int m, double alpha, double beta, const SegList& Y0, const OutList& Y);

@@ -709,3 +709,50 @@ int update_ozaki(cudaStream_t st, int64_t n, const SegList& S, const double* C, 
 }
 
 }  // namespace lob
+
+namespace lob {
+
+// Same Ozaki Gram as gram_ozaki, but with the slab count lowered until the
+// slab partials fit in work_bytes (used by the allocation-free entry point,
+// whose scratch has a fixed size).  Returns LOBPCG_ERR_ARG when even one slab
+// (p * q partials of 16 bytes) does not fit.
+int gram_ozaki_bounded(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
+                       int64_t ldg, int slices, void* work, int64_t work_bytes) {
+  const int p = U.off[U.nseg], q = V.off[V.nseg];
+  if (p <= 0 || q <= 0) return LOBPCG_OK;
+  if (slices == 0) slices = 6;
+  const int64_t per_slab = (int64_t)p * q * (int64_t)sizeof(float4);
+  if (per_slab > work_bytes) return LOBPCG_ERR_ARG;
+  int slabs;
+  int64_t rps;
+  gram_plan(n, p, q, &slabs, &rps);
+  const int64_t cap = work_bytes / per_slab;
+  if (slabs > cap) {
+    slabs = (int)cap;
+    rps = round_up(ceil_div(std::max<int64_t>(n, 1), slabs), KC);
+    slabs = (int)std::max<int64_t>(1, ceil_div(std::max<int64_t>(n, 1), rps));
+  }
+  float4* partial = (float4*)work;
+  int rc;
+  if (n <= 0) {
+    LOB_CUDA_OK(cudaMemsetAsync(partial, 0, (size_t)per_slab, st));
+    slabs = 1;
+    rc = LOBPCG_OK;
+  } else {
+    switch (slices) {
+      case 3: rc = gram_launch<3>(st, n, U, p, V, q, slabs, rps, partial); break;
+      case 4: rc = gram_launch<4>(st, n, U, p, V, q, slabs, rps, partial); break;
+      case 5: rc = gram_launch<5>(st, n, U, p, V, q, slabs, rps, partial); break;
+      case 6: rc = gram_launch<6>(st, n, U, p, V, q, slabs, rps, partial); break;
+      case 7: rc = gram_launch<7>(st, n, U, p, V, q, slabs, rps, partial); break;
+      default: return LOBPCG_ERR_ARG;
+    }
+  }
+  if (rc) return rc;
+  ozaki_slab_reduce_kernel<<<(unsigned)ceil_div((int64_t)p * q, 256), 256, 0, st>>>(
+      partial, slabs, p, q, G, ldg);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
+}  // namespace lob
