@@ -122,6 +122,100 @@ __global__ void small_stats_kernel(const double* G, int rows, int cols, int ldg,
   }
 }
 
+// cond(R) = sqrt(lambda_max(M) / lambda_min(M)) for M = R^T R (R upper, from
+// potrf), estimated in one CTA: 16 power iterations for lambda_max(M) and 16
+// for lambda_max(M^-1) = 1/lambda_min(M), the latter through the two
+// triangular solves with R.  FP32 arithmetic: the value only feeds the
+// order-of-magnitude test cond(R)^-3 < tau_skip.  out[0] = cond estimate.
+__global__ void __launch_bounds__(256) cond_estimate_kernel(int n, const double* M, int ldm,
+                                                            const double* R, int ldr,
+                                                            double* out) {
+  extern __shared__ float sh[];
+  float* x = sh;          // n
+  float* y = sh + n;      // n
+  __shared__ float red[256];
+  __shared__ float lmax_s;
+  const int tid = threadIdx.x;
+  auto block_sum = [&](float v) -> float {
+    red[tid] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    const float r = red[0];
+    __syncthreads();
+    return r;
+  };
+  // lambda_max(M)
+  for (int i = tid; i < n; i += 256) x[i] = 1.0f + 0.001f * (float)(i % 7);
+  __syncthreads();
+  float lam = 1.0f;
+  for (int it = 0; it < 16; ++it) {
+    for (int i = tid; i < n; i += 256) {
+      float s = 0.f;
+      for (int j = 0; j < n; ++j) s += (float)M[i + (int64_t)j * ldm] * x[j];
+      y[i] = s;
+    }
+    __syncthreads();
+    float nx = 0.f, ny = 0.f, nn = 0.f;
+    for (int i = tid; i < n; i += 256) {
+      nx += x[i] * y[i];
+      ny += y[i] * y[i];
+      nn += x[i] * x[i];
+    }
+    const float xy = block_sum(nx), yy = block_sum(ny), xx = block_sum(nn);
+    if (xx > 0.f) lam = fmaxf(lam, xy / xx);  // Rayleigh quotient
+    const float inv = yy > 0.f ? rsqrtf(yy) : 0.f;
+    for (int i = tid; i < n; i += 256) x[i] = y[i] * inv;
+    __syncthreads();
+  }
+  if (tid == 0) lmax_s = lam;
+  // lambda_max(M^-1) by x <- R^-1 R^-T x
+  for (int i = tid; i < n; i += 256) x[i] = 1.0f - 0.002f * (float)(i % 5);
+  __syncthreads();
+  float mu = 0.f;
+  bool bad = false;
+  for (int it = 0; it < 16 && !bad; ++it) {
+    // y = R^-T x: forward substitution, column-oriented (R^T lower)
+    for (int i = tid; i < n; i += 256) y[i] = x[i];
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+      const float rii = (float)R[i + (int64_t)i * ldr];
+      const float yi = y[i] / rii;
+      __syncthreads();
+      for (int j = i + 1 + tid; j < n; j += 256) y[j] -= (float)R[i + (int64_t)j * ldr] * yi;
+      if (tid == 0) y[i] = yi;
+      __syncthreads();
+    }
+    // x = R^-1 y: back substitution, column-oriented
+    for (int i = n - 1; i >= 0; --i) {
+      const float rii = (float)R[i + (int64_t)i * ldr];
+      const float yi = y[i] / rii;
+      __syncthreads();
+      for (int j = tid; j < i; j += 256) y[j] -= (float)R[j + (int64_t)i * ldr] * yi;
+      if (tid == 0) y[i] = yi;
+      __syncthreads();
+    }
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int i = tid; i < n; i += 256) {
+      a += x[i] * y[i];
+      b += y[i] * y[i];
+      c += x[i] * x[i];
+    }
+    const float xy = block_sum(a), yy = block_sum(b), xx = block_sum(c);
+    if (!(yy > 0.f) || !isfinite(yy)) bad = true;
+    if (xx > 0.f) mu = fmaxf(mu, xy / xx);
+    const float inv = (yy > 0.f && isfinite(yy)) ? rsqrtf(yy) : 0.f;
+    for (int i = tid; i < n; i += 256) x[i] = y[i] * inv;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double lmin = (bad || !(mu > 0.f)) ? 0.0 : 1.0 / (double)mu;
+    out[0] = lmin > 0.0 ? sqrt((double)lmax_s / lmin) : INFINITY;
+  }
+}
+
 // ------------------------------------------------------------------ helpers
 
 static unsigned blocks_for(int64_t total) { return (unsigned)std::max<int64_t>(1, ceil_div(total, 256)); }
@@ -287,16 +381,22 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
     scale_sym_kernel<<<blocks_for((int64_t)ns * ns), 256, 0, L.st>>>(ns, SAS, ns, L.d, H, ld);
     LAUNCH_OK(L);
     if ((rc = copy_mat(L, ns, ns, Rm, ld, Tz, ld))) return rc;
-    if ((rc = syevd(L, false, ns, Tz, ld))) return rc;
     SOL_OK(cusolverDnDpotrf(L.sol, CUBLAS_FILL_MODE_UPPER, ns, Rm, ld, L.work, L.lwork, L.info));
-    LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.ev, ns * sizeof(double), cudaMemcpyDeviceToHost, L.st));
-    LOB_CUDA_OK(cudaMemcpyAsync(L.host + ns, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+    LOB_CUDA_OK(cudaMemcpyAsync(L.host + 1, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
     LOB_CUDA_OK(cudaStreamSynchronize(L.st));
     int info;
-    memcpy(&info, L.host + ns, sizeof(int));
-    const double lo = L.host[0], hi = L.host[ns - 1];
-    *condR = lo > 0 ? sqrt(hi / lo) : INFINITY;
-    if (info != 0 || !(pow(*condR, -3.0) >= tau_skip)) {
+    memcpy(&info, L.host + 1, sizeof(int));
+    if (info != 0) {
+      *flip = true;
+      *condR = INFINITY;
+      return LOBPCG_OK;
+    }
+    cond_estimate_kernel<<<1, 256, 2 * ns * sizeof(float), L.st>>>(ns, Tz, ld, Rm, ld, L.scal);
+    LAUNCH_OK(L);
+    double cr;
+    if ((rc = to_host(L, &cr, L.scal, sizeof(double)))) return rc;
+    *condR = cr;
+    if (!(pow(*condR, -3.0) >= tau_skip)) {
       *flip = true;
       return LOBPCG_OK;
     }

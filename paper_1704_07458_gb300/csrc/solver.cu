@@ -197,11 +197,11 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   for (int p = 1; p <= nsmax; ++p)
     for (int q = 1; q <= 2 * nx; ++q) {
       gb = std::max(gb, gram_f64_workspace(n, p, q));
-      if (mode) gb = std::max(gb, gram_ozaki_workspace(n, p, q, sl));
+      if (mode) gb = std::max(gb, gram_ozaki_workspace(n, p, q, std::max(sl, 7)));
     }
   h->gwork_bytes = gb;
   if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
-  h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), sl) : 0;
+  h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)) : 0;
   if (h->uwork_bytes > 0 && (rc = dalloc(h, &h->uwork, (size_t)h->uwork_bytes))) return rc;
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
@@ -216,23 +216,29 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
 
 // ---- thin wrappers choosing the arithmetic of the dense contractions
 
-int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t ldg) {
+// min_slices: the orthogonality tests of Algorithm 5 compare ||U^T B U - I||
+// with 100 eps, which needs the 7-slice (2^-56) split; the projected pencil
+// does not.
+int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t ldg,
+         int min_slices = 0) {
   h->stats.gram_calls++;
   h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
   if (gemm_mode(h))
-    return gram_ozaki(h->st, h->n, U, V, G, ldg, slices(h), h->gwork, h->gwork_bytes);
+    return gram_ozaki(h->st, h->n, U, V, G, ldg, std::max(slices(h), min_slices), h->gwork,
+                      h->gwork_bytes);
   return gram_f64(h->st, h->n, U, V, G, ldg, h->gwork, h->gwork_bytes);
 }
 
 // colexp: per-column power-of-two balance of S for the tensor-core path (see
 // update_ozaki); h->zexp when the columns of S are already balanced.
 int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m, double alpha,
-           double beta, const SegList& Y0, const OutList& Y, const int* colexp) {
+           double beta, const SegList& Y0, const OutList& Y, const int* colexp,
+           int min_slices = 0) {
   h->stats.update_calls++;
   h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
   if (gemm_mode(h))
-    return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y, slices(h), h->uwork,
-                        h->uwork_bytes, colexp);
+    return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
+                        std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);
   return update_f64(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y);
 }
 
@@ -320,10 +326,10 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
   double st3[3];
   for (int i = 0; i < 3 && nu > 0; ++i) {
     // U = U - V (V^T B U), with V^T B U formed as (BV)^T U
-    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv))) return rc;
+    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv, 7))) return rc;
     double* dst = spare(Ubase, nullptr);
     if ((rc = update(h, V, h->Gs, nv, nu, -1.0, 1.0, seg1(U, h->ld, nu), out1(dst, h->ld, nu),
-                     h->zexp)))
+                     h->zexp, 7)))
       return rc;
     U = Ubase = dst;
     for (int j = 0; j < 3; ++j) {
@@ -332,7 +338,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
         if ((rc = apply_B(h, U, nu, BU))) return rc;
         BUp = BU;
       }
-      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu))) return rc;
+      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu, 7))) return rc;
       if ((rc = diag_exponents(h->st, nu, h->Gs, nu, h->cexp))) return rc;
       int keep = 0;
       {
@@ -346,7 +352,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
       }
       dst = spare(Ubase, nullptr);
       if ((rc = update(h, seg1(U, h->ld, nu), h->Cm, nu, keep, 1.0, 0.0, seg_empty(),
-                       out1(dst, h->ld, keep), h->cexp)))
+                       out1(dst, h->ld, keep), h->cexp, 7)))
         return rc;
       U = Ubase = dst;
       nu = keep;
@@ -355,7 +361,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
         if ((rc = apply_B(h, U, nu, BU))) return rc;
         BUp = BU;
       }
-      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu))) return rc;
+      if ((rc = gram(h, seg1(U, h->ld, nu), seg1(BUp, h->ld, nu), h->Gs, nu, 7))) return rc;
       if ((rc = colsumsq(h->st, h->n, U, h->ld, nu, h->colA, h->rwork))) return rc;
       if ((rc = colsumsq(h->st, h->n, BUp, h->ld, nu, h->colB, h->rwork))) return rc;
       if ((rc = small_stats(h->dense, h->Gs, nu, nu, nu, true, h->colA, nu, h->colB, nu, st3)))
@@ -364,7 +370,7 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
       if (err <= tau_ortho) break;
     }
     if (nu == 0 || nv == 0) break;
-    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv))) return rc;
+    if ((rc = gram(h, BV, seg1(U, h->ld, nu), h->Gs, nv, 7))) return rc;
     if ((rc = colsumsq(h->st, h->n, U, h->ld, nu, h->colA, h->rwork))) return rc;
     if ((rc = small_stats(h->dense, h->Gs, nv, nu, nv, false, h->colA, nu, h->colA, 0, st3)))
       return rc;
@@ -386,7 +392,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
                                       : k + std::max<int64_t>((k + 9) / 10, 2);
   nx = std::min(nx, n);
   if (nx < k) return h->fail(LOBPCG_ERR_ARG, "block_width < k");
-  if (3 * nx > 65536) return h->fail(LOBPCG_ERR_ARG, "block too wide");
+  if (3 * nx > 6144) return h->fail(LOBPCG_ERR_ARG, "block too wide (3 n_x > 6144)");
   if (!lambda || !Xout || ldx < k) return h->fail(LOBPCG_ERR_ARG, "bad output buffers");
   if (X0 && ldx0 < nx) return h->fail(LOBPCG_ERR_ARG, "ldx0 < block width");
   if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
