@@ -48,8 +48,9 @@ typedef enum { LOBPCG_MEM_HOST = 0, LOBPCG_MEM_DEVICE = 1 } lobpcg_mem;
 /* Arithmetic used for the n-scaled dense contractions (Gram S^T Y and basis
  * update S C).  Both give FP64-accurate results; see lobpcg_gram. */
 typedef enum {
-  LOBPCG_GEMM_F64 = 0,     /* plain FP64 fused multiply-add on the CUDA cores */
-  LOBPCG_GEMM_OZAKI = 1    /* FP64 emulated by exact BF16 splits on the tensor cores */
+  LOBPCG_GEMM_F64 = 0,      /* plain FP64 fused multiply-add on the CUDA cores */
+  LOBPCG_GEMM_OZAKI = 1,    /* FP64 emulated by exact BF16 splits, warp-level mma.sync */
+  LOBPCG_GEMM_OZAKI_TC = 2  /* same splits; Grams on tcgen05 with TMEM accumulators */
 } lobpcg_gemm_mode;
 
 /* Options; zero-initialise and set what you need, zeros select the defaults

@@ -16,7 +16,7 @@ from . import _native
 from ._native import (  # noqa: F401
     LOBPCG_OK, LOBPCG_ERR_ARG, LOBPCG_ERR_NOT_CONVERGED, LOBPCG_ERR_BREAKDOWN,
     LOBPCG_ERR_CUDA, LOBPCG_ERR_OOM, LOBPCG_ERR_TIMEOUT, LOBPCG_ERR_CALLBACK,
-    LOBPCG_MEM_HOST, LOBPCG_MEM_DEVICE, LOBPCG_GEMM_F64, LOBPCG_GEMM_OZAKI,
+    LOBPCG_MEM_HOST, LOBPCG_MEM_DEVICE, LOBPCG_GEMM_F64, LOBPCG_GEMM_OZAKI, LOBPCG_GEMM_OZAKI_TC,
     lobpcg_options_t, lobpcg_stats_t, LobpcgError,
     lobpcg_create, lobpcg_set_operator, lobpcg_set_precond_diag,
     lobpcg_set_precond_callback, lobpcg_solve, lobpcg_get_stats, lobpcg_last_error,
@@ -34,7 +34,8 @@ def options(**kw):
     o = lobpcg_options_t()
     for k, v in kw.items():
         if k == "gemm_mode" and isinstance(v, str):
-            v = {"f64": LOBPCG_GEMM_F64, "ozaki": LOBPCG_GEMM_OZAKI}[v]
+            v = {"f64": LOBPCG_GEMM_F64, "ozaki": LOBPCG_GEMM_OZAKI,
+                 "ozaki_tc": LOBPCG_GEMM_OZAKI_TC}[v]
         if k == "implicit" and isinstance(v, str):
             v = {"auto": 0, "never": 1, "always": 2}[v]
         setattr(o, k, v)

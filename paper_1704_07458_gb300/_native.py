@@ -21,6 +21,7 @@ LOBPCG_MEM_HOST = 0
 LOBPCG_MEM_DEVICE = 1
 LOBPCG_GEMM_F64 = 0
 LOBPCG_GEMM_OZAKI = 1
+LOBPCG_GEMM_OZAKI_TC = 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_CONVERGED", 3: "ERR_BREAKDOWN",
                 4: "ERR_CUDA", 5: "ERR_OOM", 6: "ERR_TIMEOUT", 7: "ERR_CALLBACK"}

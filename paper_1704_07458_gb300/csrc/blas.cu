@@ -479,6 +479,9 @@ LOBPCG_EXPORT int64_t lobpcg_gram_workspace(int64_t n, int64_t p, int64_t q, int
                                             int slices) {
   if (n < 0 || p < 0 || q < 0) return -1;
   if (mode == LOBPCG_GEMM_OZAKI) return lob::gram_ozaki_workspace(n, (int)p, (int)q, slices);
+  if (mode == LOBPCG_GEMM_OZAKI_TC)
+    return std::max(lob::gram_tc_workspace(n, (int)p, (int)q),
+                    lob::gram_ozaki_workspace(n, (int)p, (int)q, slices));
   return lob::gram_f64_workspace(n, (int)p, (int)q);
 }
 
@@ -490,7 +493,8 @@ LOBPCG_EXPORT int lobpcg_gram(int64_t n, const double* U, int64_t ldu, int64_t p
   if (p == 0 || q == 0) return LOBPCG_OK;
   if (!G || ldg < p || (n > 0 && (!seg_ok(U, ldu, p) || !seg_ok(V, ldv, q))))
     return LOBPCG_ERR_ARG;
-  if (mode != LOBPCG_GEMM_F64 && mode != LOBPCG_GEMM_OZAKI) return LOBPCG_ERR_ARG;
+  if (mode != LOBPCG_GEMM_F64 && mode != LOBPCG_GEMM_OZAKI && mode != LOBPCG_GEMM_OZAKI_TC)
+    return LOBPCG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t need = lobpcg_gram_workspace(n, p, q, mode, slices);
   void* own = nullptr;
@@ -501,9 +505,11 @@ LOBPCG_EXPORT int lobpcg_gram(int64_t n, const double* U, int64_t ldu, int64_t p
     work_bytes = need;
   }
   lob::SegList Us = lob::seg1(U, ldu, (int)p), Vs = lob::seg1(V, ldv, (int)q);
-  int rc = mode == LOBPCG_GEMM_OZAKI
-               ? lob::gram_ozaki(st, n, Us, Vs, G, ldg, slices, work, work_bytes)
-               : lob::gram_f64(st, n, Us, Vs, G, ldg, work, work_bytes);
+  int rc = mode == LOBPCG_GEMM_OZAKI_TC
+               ? lob::gram_tc(st, n, Us, Vs, G, ldg, slices, work, work_bytes)
+               : mode == LOBPCG_GEMM_OZAKI
+                     ? lob::gram_ozaki(st, n, Us, Vs, G, ldg, slices, work, work_bytes)
+                     : lob::gram_f64(st, n, Us, Vs, G, ldg, work, work_bytes);
   if (own) cudaFreeAsync(own, st);
   return rc;
 }
@@ -516,12 +522,13 @@ LOBPCG_EXPORT int lobpcg_update(int64_t n, const double* S, int64_t lds, int64_t
   if (n == 0 || m == 0) return LOBPCG_OK;
   if (!Y || ldy < m || (s > 0 && (!seg_ok(S, lds, s) || !C || ldc < s))) return LOBPCG_ERR_ARG;
   if (beta != 0.0 && !seg_ok(Y0, ldy0, m)) return LOBPCG_ERR_ARG;
-  if (mode != LOBPCG_GEMM_F64 && mode != LOBPCG_GEMM_OZAKI) return LOBPCG_ERR_ARG;
+  if (mode != LOBPCG_GEMM_F64 && mode != LOBPCG_GEMM_OZAKI && mode != LOBPCG_GEMM_OZAKI_TC)
+    return LOBPCG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   lob::SegList Ss = s > 0 ? lob::seg1(S, lds, (int)s) : lob::seg_empty();
   lob::SegList Y0s = beta != 0.0 ? lob::seg1(Y0, ldy0, (int)m) : lob::seg_empty();
   lob::OutList out{{Y, Y}, {ldy, ldy}, (int)m};
-  if (mode == LOBPCG_GEMM_OZAKI) {
+  if (mode == LOBPCG_GEMM_OZAKI || mode == LOBPCG_GEMM_OZAKI_TC) {
     const int64_t need = lob::update_ozaki_workspace(n, (int)s, (int)m, slices);
     void* own = nullptr;
     if (need > 0 && cudaMallocAsync(&own, (size_t)need, st) != cudaSuccess) return LOBPCG_ERR_OOM;

@@ -20,6 +20,15 @@ int64_t gram_ozaki_workspace(int64_t n, int p, int q, int slices);
 int gram_ozaki(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
                int64_t ldg, int slices, void* work, int64_t work_bytes);
 
+// Fixed-order sum of Ozaki slab partials (hi, lo, exponent) into G (column-major).
+int ozaki_slab_reduce(cudaStream_t st, const float4* partial, int slabs, int p, int q, double* G,
+                      int64_t ldg);
+
+// Same Gram on the tcgen05 tensor cores with TMEM accumulators (ozaki_tc.cu).
+int64_t gram_tc_workspace(int64_t n, int p, int q);
+int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
+            int64_t ldg, int slices, void* work, int64_t work_bytes);
+
 // As gram_ozaki, with as many row slabs as fit in work_bytes (fixed scratch).
 int gram_ozaki_bounded(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
                        int64_t ldg, int slices, void* work, int64_t work_bytes);

@@ -639,6 +639,15 @@ int update_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const do
 
 }  // namespace
 
+int ozaki_slab_reduce(cudaStream_t st, const float4* partial, int slabs, int p, int q, double* G,
+                      int64_t ldg) {
+  const int64_t tot = (int64_t)p * q;
+  ozaki_slab_reduce_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(partial, slabs, p, q, G,
+                                                                         ldg);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
 int64_t gram_ozaki_workspace(int64_t n, int p, int q, int) {
   int slabs;
   int64_t r;

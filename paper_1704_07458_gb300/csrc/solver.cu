@@ -153,7 +153,11 @@ int dalloc(lobpcg_ctx* h, void** p, size_t bytes) {
   return LOBPCG_OK;
 }
 
-int gemm_mode(const lobpcg_ctx* h) { return h->opt.gemm_mode == LOBPCG_GEMM_OZAKI ? 1 : 0; }
+int gemm_mode(const lobpcg_ctx* h) {
+  return (h->opt.gemm_mode == LOBPCG_GEMM_OZAKI || h->opt.gemm_mode == LOBPCG_GEMM_OZAKI_TC)
+             ? h->opt.gemm_mode
+             : 0;
+}
 int slices(const lobpcg_ctx* h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : 6; }
 
 int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
@@ -198,6 +202,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
     for (int q = 1; q <= 2 * nx; ++q) {
       gb = std::max(gb, gram_f64_workspace(n, p, q));
       if (mode) gb = std::max(gb, gram_ozaki_workspace(n, p, q, std::max(sl, 7)));
+      if (mode == LOBPCG_GEMM_OZAKI_TC) gb = std::max(gb, gram_tc_workspace(n, p, q));
     }
   h->gwork_bytes = gb;
   if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
@@ -223,6 +228,9 @@ int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t l
          int min_slices = 0) {
   h->stats.gram_calls++;
   h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
+  if (gemm_mode(h) == LOBPCG_GEMM_OZAKI_TC)
+    return gram_tc(h->st, h->n, U, V, G, ldg, std::max(slices(h), min_slices), h->gwork,
+                   h->gwork_bytes);
   if (gemm_mode(h))
     return gram_ozaki(h->st, h->n, U, V, G, ldg, std::max(slices(h), min_slices), h->gwork,
                       h->gwork_bytes);
@@ -706,7 +714,8 @@ LOBPCG_EXPORT int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, voi
   auto* h = new (std::nothrow) lobpcg_ctx();
   if (!h) return LOBPCG_ERR_OOM;
   if (opts) h->opt = *opts;
-  if (h->opt.gemm_mode != LOBPCG_GEMM_F64 && h->opt.gemm_mode != LOBPCG_GEMM_OZAKI) {
+  if (h->opt.gemm_mode != LOBPCG_GEMM_F64 && h->opt.gemm_mode != LOBPCG_GEMM_OZAKI &&
+      h->opt.gemm_mode != LOBPCG_GEMM_OZAKI_TC) {
     delete h;
     return LOBPCG_ERR_ARG;
   }

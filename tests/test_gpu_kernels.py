@@ -15,7 +15,8 @@ from gpu_util import torch_cuda, dev, host, dev_i32, gamma
 pytestmark = pytest.mark.gpu
 
 MODES = [(gb.LOBPCG_GEMM_F64, 0), (gb.LOBPCG_GEMM_OZAKI, 6), (gb.LOBPCG_GEMM_OZAKI, 4),
-         (gb.LOBPCG_GEMM_OZAKI, 7)]
+         (gb.LOBPCG_GEMM_OZAKI, 7), (gb.LOBPCG_GEMM_OZAKI_TC, 6), (gb.LOBPCG_GEMM_OZAKI_TC, 4),
+         (gb.LOBPCG_GEMM_OZAKI_TC, 7)]
 
 
 def ozaki_unit(slices):
@@ -94,7 +95,7 @@ def test_gram_parity(n, p, q, mode, slices):
     got = host(G).reshape(q, p + 3).T[:p, :]
     ref = ok.gram(U, V)
     bound = 2 * gamma(n) * (np.abs(U).T @ np.abs(V))
-    if mode == gb.LOBPCG_GEMM_OZAKI:
+    if mode != gb.LOBPCG_GEMM_F64:
         # per 64-row chunk c: unit * 64 * max_c|u_i| * max_c|v_j| (2x for the exponent bound)
         nck = (n + 63) // 64
         mu = np.zeros((nck, p)); mv = np.zeros((nck, q))
@@ -121,7 +122,7 @@ def test_update_parity(n, s, m, beta, mode, slices):
     assert rc == 0
     ref = beta * Y0 - ok.update(S, C)
     bound = 2 * gamma(s + 1) * (np.abs(S) @ np.abs(C) + abs(beta) * np.abs(Y0))
-    if mode == gb.LOBPCG_GEMM_OZAKI:
+    if mode != gb.LOBPCG_GEMM_F64:
         # columns of S balanced by 2^E_k (E_k its exponent bound), rows of C by 2^-E_k:
         # the balanced S has entries below 1, the balanced C entries below 2 max|S_k| |C_kj|
         Ct = np.abs(C) * (2 * np.abs(S).max(0))[:, None]

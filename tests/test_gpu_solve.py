@@ -12,7 +12,7 @@ from gpu_util import torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["f64", "ozaki"]
+MODES = ["f64", "ozaki", "ozaki_tc"]
 
 
 def _oracle(p, seed=0, nx=None, opts=None):
