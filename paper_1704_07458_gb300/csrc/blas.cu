@@ -529,11 +529,15 @@ LOBPCG_EXPORT int lobpcg_update(int64_t n, const double* S, int64_t lds, int64_t
   lob::SegList Y0s = beta != 0.0 ? lob::seg1(Y0, ldy0, (int)m) : lob::seg_empty();
   lob::OutList out{{Y, Y}, {ldy, ldy}, (int)m};
   if (mode == LOBPCG_GEMM_OZAKI || mode == LOBPCG_GEMM_OZAKI_TC) {
-    const int64_t need = lob::update_ozaki_workspace(n, (int)s, (int)m, slices);
+    const bool tc = mode == LOBPCG_GEMM_OZAKI_TC;
+    const int64_t need = tc ? lob::update_tc_workspace(n, (int)s, (int)m, slices)
+                            : lob::update_ozaki_workspace(n, (int)s, (int)m, slices);
     void* own = nullptr;
     if (need > 0 && cudaMallocAsync(&own, (size_t)need, st) != cudaSuccess) return LOBPCG_ERR_OOM;
-    int rc = lob::update_ozaki(st, n, Ss, C, ldc, (int)m, alpha, beta, Y0s, out, slices, own,
-                               need);
+    int rc = tc ? lob::update_tc(st, n, Ss, C, ldc, (int)m, alpha, beta, Y0s, out, slices, own,
+                                 need)
+                : lob::update_ozaki(st, n, Ss, C, ldc, (int)m, alpha, beta, Y0s, out, slices,
+                                    own, need);
     if (own) cudaFreeAsync(own, st);
     return rc;
   }

@@ -123,16 +123,20 @@ __global__ void small_stats_kernel(const double* G, int rows, int cols, int ldg,
 }
 
 // cond(R) = sqrt(lambda_max(M) / lambda_min(M)) for M = R^T R (R upper, from
-// potrf), estimated in one CTA: 16 power iterations for lambda_max(M) and 16
-// for lambda_max(M^-1) = 1/lambda_min(M), the latter through the two
-// triangular solves with R.  FP32 arithmetic: the value only feeds the
-// order-of-magnitude test cond(R)^-3 < tau_skip.  out[0] = cond estimate.
+// potrf), estimated in one CTA: power iterations for lambda_max(M) and for
+// lambda_max(M^-1) = 1/lambda_min(M), the latter through the two triangular
+// solves with R.  FP32 arithmetic: the value only feeds the order-of-
+// magnitude test cond(R)^-3 < tau_skip.  R is staged in shared memory when it
+// fits (rstage != 0).  out[0] = cond estimate.
+constexpr int kCondIters = 8;
+
 __global__ void __launch_bounds__(256) cond_estimate_kernel(int n, const double* M, int ldm,
-                                                            const double* R, int ldr,
+                                                            const double* R, int ldr, int rstage,
                                                             double* out) {
   extern __shared__ float sh[];
   float* x = sh;          // n
   float* y = sh + n;      // n
+  float* Rs = sh + 2 * n; // n x n (column-major) when staged
   __shared__ float red[256];
   __shared__ float lmax_s;
   const int tid = threadIdx.x;
@@ -147,11 +151,19 @@ __global__ void __launch_bounds__(256) cond_estimate_kernel(int n, const double*
     __syncthreads();
     return r;
   };
+  if (rstage)
+    for (int64_t e = tid; e < (int64_t)n * n; e += 256) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      Rs[e] = i <= j ? (float)R[i + (int64_t)j * ldr] : 0.f;
+    }
+  auto Rij = [&](int i, int j) -> float {
+    return rstage ? Rs[i + (int64_t)j * n] : (float)R[i + (int64_t)j * ldr];
+  };
   // lambda_max(M)
   for (int i = tid; i < n; i += 256) x[i] = 1.0f + 0.001f * (float)(i % 7);
   __syncthreads();
   float lam = 1.0f;
-  for (int it = 0; it < 16; ++it) {
+  for (int it = 0; it < kCondIters; ++it) {
     for (int i = tid; i < n; i += 256) {
       float s = 0.f;
       for (int j = 0; j < n; ++j) s += (float)M[i + (int64_t)j * ldm] * x[j];
@@ -176,24 +188,22 @@ __global__ void __launch_bounds__(256) cond_estimate_kernel(int n, const double*
   __syncthreads();
   float mu = 0.f;
   bool bad = false;
-  for (int it = 0; it < 16 && !bad; ++it) {
+  for (int it = 0; it < kCondIters && !bad; ++it) {
     // y = R^-T x: forward substitution, column-oriented (R^T lower)
     for (int i = tid; i < n; i += 256) y[i] = x[i];
     __syncthreads();
     for (int i = 0; i < n; ++i) {
-      const float rii = (float)R[i + (int64_t)i * ldr];
-      const float yi = y[i] / rii;
+      const float yi = y[i] / Rij(i, i);
       __syncthreads();
-      for (int j = i + 1 + tid; j < n; j += 256) y[j] -= (float)R[i + (int64_t)j * ldr] * yi;
+      for (int j = i + 1 + tid; j < n; j += 256) y[j] -= Rij(i, j) * yi;
       if (tid == 0) y[i] = yi;
       __syncthreads();
     }
     // x = R^-1 y: back substitution, column-oriented
     for (int i = n - 1; i >= 0; --i) {
-      const float rii = (float)R[i + (int64_t)i * ldr];
-      const float yi = y[i] / rii;
+      const float yi = y[i] / Rij(i, i);
       __syncthreads();
-      for (int j = tid; j < i; j += 256) y[j] -= (float)R[j + (int64_t)i * ldr] * yi;
+      for (int j = tid; j < i; j += 256) y[j] -= Rij(j, i) * yi;
       if (tid == 0) y[i] = yi;
       __syncthreads();
     }
@@ -391,8 +401,20 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
       *condR = INFINITY;
       return LOBPCG_OK;
     }
-    cond_estimate_kernel<<<1, 256, 2 * ns * sizeof(float), L.st>>>(ns, Tz, ld, Rm, ld, L.scal);
-    LAUNCH_OK(L);
+    {
+      // stage R in shared memory when it fits (227 KB per block)
+      const size_t full = (size_t)(2 * ns + (size_t)ns * ns) * sizeof(float);
+      const int rstage = full <= 200 * 1024 ? 1 : 0;
+      const size_t bytes = rstage ? full : 2 * ns * sizeof(float);
+      static bool configured = false;
+      if (!configured) {
+        LOB_CUDA_OK(cudaFuncSetAttribute(cond_estimate_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured = true;
+      }
+      cond_estimate_kernel<<<1, 256, bytes, L.st>>>(ns, Tz, ld, Rm, ld, rstage, L.scal);
+      LAUNCH_OK(L);
+    }
     double cr;
     if ((rc = to_host(L, &cr, L.scal, sizeof(double)))) return rc;
     *condR = cr;

@@ -29,6 +29,15 @@ int64_t gram_tc_workspace(int64_t n, int p, int q);
 int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
             int64_t ldg, int slices, void* work, int64_t work_bytes);
 
+// Y = beta Y0 + alpha S C on tcgen05 (beta 0 or 1), colexp as update_ozaki.
+int64_t update_tc_workspace(int64_t n, int s, int m, int slices);
+int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc, int m,
+              double alpha, double beta, const SegList& Y0, const OutList& Y, int slices,
+              void* work, int64_t work_bytes, const int* colexp = nullptr);
+
+// colexp[k] = E with max_i |S(i, k)| < 2^E over an n x s block (0 for zero columns).
+int column_exponents(cudaStream_t st, int64_t n, const SegList& Sg, int s, int* out);
+
 // As gram_ozaki, with as many row slabs as fit in work_bytes (fixed scratch).
 int gram_ozaki_bounded(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
                        int64_t ldg, int slices, void* work, int64_t work_bytes);

@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "ozaki_common.cuh"
 
 namespace lob {
 namespace {
@@ -183,6 +184,117 @@ __device__ __forceinline__ void stage_core(const double* col, int64_t ld, int64_
     *reinterpret_cast<uint4*>(dst + s * plane_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
+// Phase A (exact levels 2, 3, 4), flush of level 4, phase B (levels 5..S+1 in
+// the same columns), flush of everything into (hi, lo).  The planes of the
+// chunk are in shared memory and fenced.  Returns true if an MMA completion
+// was not observed within the bounded wait.
+template <int S>
+__device__ __forceinline__ bool tc_mma_and_flush(TcShared& sh, int tid, int warp, int lane,
+                                                 int my_row, int col0, uint32_t aBase,
+                                                 uint32_t bBase, uint32_t idesc, uint32_t acc2,
+                                                 uint32_t acc3, uint32_t accl, uint32_t& phase,
+                                                 float (&hi)[72], float (&lo)[72]) {
+  // phase A (one thread): exact levels 2, 3 and 4
+  const uint32_t lboA = (TCM / 8) * 128, lboB = (TCN / 8) * 128, sbo = 128;
+  const uint32_t planeA_bytes = KG * (TCM / 8) * 128, planeB_bytes = KG * (TCN / 8) * 128;
+  auto issue = [&](uint32_t acc, int si, int ti, bool first) {
+#pragma unroll
+    for (int ks = 0; ks < TCK / 16; ++ks) {
+      // K offset ks*16 = two core-matrix groups
+      const uint64_t a = smem_desc(aBase + si * planeA_bytes + ks * 2 * lboA, lboA, sbo);
+      const uint64_t b = smem_desc(bBase + ti * planeB_bytes + ks * 2 * lboB, lboB, sbo);
+      mma_bf16_tc(acc, a, b, idesc, (first && ks == 0) ? 0u : 1u);
+    }
+  };
+  auto issue_level = [&](uint32_t acc, int L, bool first) {
+    for (int si = max(1, L - S); si <= min(S, L - 1); ++si) {
+      issue(acc, si - 1, L - si - 1, first);
+      first = false;
+    }
+  };
+  auto commit_and_wait = [&]() -> bool {
+    if (tid == 0)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_u32(&sh.mbar)));
+    uint32_t done = 0;
+    for (int spin = 0; spin < (1 << 22) && !done; ++spin) {
+      asm volatile(
+          "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+          "selp.b32 %0, 1, 0, P;\n\t}\n"
+          : "=r"(done)
+          : "r"(smem_u32(&sh.mbar)), "r"(phase));
+    }
+    phase ^= 1u;
+    const bool bad = __syncthreads_or(!done);
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    return bad;
+  };
+  const float sa = p2f(sh.eA[my_row] - sh.rA[my_row] - 14);
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  auto flush1 = [&](uint32_t acc) {
+#pragma unroll
+    for (int cb = 0; cb < 72; cb += 8) {
+      float v[8];
+      tmem_ld8(acc + lane_off + col0 + cb, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        two_sum_acc(hi[cb + i], lo[cb + i], v[i] * (sa * sh.sB[col0 + cb + i]));
+    }
+  };
+  if (sh.rescale) {
+    const float fa = p2f(max(sh.dA[my_row], -127));
+#pragma unroll
+    for (int j = 0; j < 72; ++j) {
+      const float f = fa * p2f(max(sh.dB[min(col0 + j, TCN - 1)], -127));
+      hi[j] *= f;
+      lo[j] *= f;
+    }
+  }
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    issue_level(acc2, 2, true);
+    issue_level(acc3, 3, true);
+    if (S >= 3) issue_level(accl, 4, true);
+  }
+  if (commit_and_wait()) {
+    return true;
+  }
+  if (S >= 3) flush1(accl);
+  // further phases into the same columns: for S = 7 level 5 gets its own exact
+  // phase so that the inexact tail (levels >= 6, below 2^-32 of level 2)
+  // rounds below 2^-53; otherwise levels 5 .. S+1 (below 2^-24) share one.
+  for (int L0 = 5; L0 <= S + 1;) {
+    const int L1 = (S >= 7 && L0 == 5) ? 5 : S + 1;
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      bool first = true;
+      for (int L = L0; L <= L1; ++L) {
+        issue_level(accl, L, first);
+        first = false;
+      }
+    }
+    if (commit_and_wait()) return true;
+    flush1(accl);
+    L0 = L1 + 1;
+  }
+  flush1(acc2);
+  flush1(acc3);
+  // renormalise
+#pragma unroll
+  for (int j = 0; j < 72; ++j) {
+    const float s2 = hi[j] + lo[j];
+    lo[j] = lo[j] - (s2 - hi[j]);
+    hi[j] = s2;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+    return false;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kThr, 1)
     ozaki_gram_tc_kernel(int64_t n, SegList U, int p, SegList V, int q, int64_t rows_per_slab,
@@ -312,104 +424,11 @@ __global__ void __launch_bounds__(kThr, 1)
     // make the generic-proxy stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;\n");
     __syncthreads();
-    // ---- 3. MMAs, phase A (one thread): exact levels 2, 3 and 4
-    const uint32_t lboA = (TCM / 8) * 128, lboB = (TCN / 8) * 128, sbo = 128;
-    const uint32_t planeA_bytes = KG * (TCM / 8) * 128, planeB_bytes = KG * (TCN / 8) * 128;
-    auto issue = [&](uint32_t acc, int si, int ti, bool first) {
-#pragma unroll
-      for (int ks = 0; ks < TCK / 16; ++ks) {
-        // K offset ks*16 = two core-matrix groups
-        const uint64_t a = smem_desc(aBase + si * planeA_bytes + ks * 2 * lboA, lboA, sbo);
-        const uint64_t b = smem_desc(bBase + ti * planeB_bytes + ks * 2 * lboB, lboB, sbo);
-        mma_bf16_tc(acc, a, b, idesc, (first && ks == 0) ? 0u : 1u);
-      }
-    };
-    auto issue_level = [&](uint32_t acc, int L, bool first) {
-      for (int si = max(1, L - S); si <= min(S, L - 1); ++si) {
-        issue(acc, si - 1, L - si - 1, first);
-        first = false;
-      }
-    };
-    auto commit_and_wait = [&]() -> bool {
-      if (tid == 0)
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&sh.mbar)));
-      uint32_t done = 0;
-      for (int spin = 0; spin < (1 << 22) && !done; ++spin) {
-        asm volatile(
-            "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, P;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(&sh.mbar)), "r"(phase));
-      }
-      phase ^= 1u;
-      const bool bad = __syncthreads_or(!done);
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      return bad;
-    };
-    const float sa = p2f(sh.eA[my_row] - sh.rA[my_row] - 14);
-    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-    auto flush1 = [&](uint32_t acc) {
-#pragma unroll
-      for (int cb = 0; cb < 72; cb += 8) {
-        float v[8];
-        tmem_ld8(acc + lane_off + col0 + cb, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          two_sum_acc(hi[cb + i], lo[cb + i], v[i] * (sa * sh.sB[col0 + cb + i]));
-      }
-    };
-    if (sh.rescale) {
-      const float fa = p2f(max(sh.dA[my_row], -127));
-#pragma unroll
-      for (int j = 0; j < 72; ++j) {
-        const float f = fa * p2f(max(sh.dB[min(col0 + j, TCN - 1)], -127));
-        hi[j] *= f;
-        lo[j] *= f;
-      }
-    }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      issue_level(acc2, 2, true);
-      issue_level(acc3, 3, true);
-      if (S >= 3) issue_level(accl, 4, true);
-    }
-    if (commit_and_wait()) {
+    if (tc_mma_and_flush<S>(sh, tid, warp, lane, my_row, col0, aBase, bBase, idesc, acc2, acc3,
+                            accl, phase, hi, lo)) {
       failed = true;
       break;
     }
-    if (S >= 3) flush1(accl);
-    if (S >= 4) {
-      // ---- phase B: levels 5 .. S+1 (below 2^-24 of level 2) into the same columns
-      asm volatile("tcgen05.fence::before_thread_sync;\n");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        bool first = true;
-        for (int L = 5; L <= S + 1; ++L) {
-          issue_level(accl, L, first);
-          first = false;
-        }
-      }
-      if (commit_and_wait()) {
-        failed = true;
-        break;
-      }
-      flush1(accl);
-    }
-    flush1(acc2);
-    flush1(acc3);
-    // renormalise
-#pragma unroll
-    for (int j = 0; j < 72; ++j) {
-      const float s2 = hi[j] + lo[j];
-      lo[j] = lo[j] - (s2 - hi[j]);
-      hi[j] = s2;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
   }
   // ---- partial result (hi, lo, exponent) of this slab
   float4* out = partial + (int64_t)blockIdx.z * p * q;
@@ -425,6 +444,205 @@ __global__ void __launch_bounds__(kThr, 1)
         v.z = __int_as_float(sh.rA[my_row] + sh.rB[c]);
         v.w = 0.f;
         out[(int64_t)gi * q + (tq + c)] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+// ---------------------------------------------------------------- update
+// Y = beta Y0 + alpha S C on tcgen05.  A (M = 128 rows of S) x K (32 columns
+// of S per chunk, row exponents per chunk, columns balanced by 2^-colexp[k]);
+// B = alpha C with rows balanced by 2^colexp[k], pre-split once per call into
+// the exact shared-memory plane layout [chunk][ntile][S][KG][TCN/8][8][8] by
+// split_c_tc_kernel, with per-(chunk, column) exponents.
+
+template <int S>
+__global__ void split_c_tc_kernel(const double* __restrict__ C, int64_t ldc, int s, int m,
+                                  int ntiles, double alpha, const int* __restrict__ colexp,
+                                  uint16_t* __restrict__ Cs, int* __restrict__ Ce) {
+  // one warp per (chunk, padded column); lane = k within the chunk
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (s + TCK - 1) / TCK;
+  const int ncols = ntiles * TCN;
+  if (w >= nchunks * ncols) return;
+  const int ch = w / ncols, jj = w % ncols;
+  const int tile = jj / TCN, j = jj % TCN;
+  const int k = ch * TCK + lane;
+  double x = 0.0;
+  if (jj < m && k < s) x = ldexp(alpha * C[k + (int64_t)jj * ldc], colexp ? colexp[k] : 0);
+  int e = eff_exp0(x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  const int E = e - 1022;
+  uint16_t dg[S];
+  split_weighted<S>(x, E, dg);
+  const size_t base = (size_t)(ch * ntiles + tile) * S * KG * (TCN / 8) * 64;
+  const int kg = lane >> 3, ng = j >> 3;
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl)
+    Cs[base + (((size_t)sl * KG + kg) * (TCN / 8) + ng) * 64 + (j & 7) * 8 + (lane & 7)] = dg[sl];
+  if (lane == 0) Ce[(ch * ntiles + tile) * TCN + j] = E;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThr, 1)
+    ozaki_update_tc_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
+                           const uint16_t* __restrict__ Cs, const int* __restrict__ Ce, int m,
+                           int ntiles, double beta, SegList Y0, OutList Y) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t* planeA = reinterpret_cast<uint16_t*>(smem_raw);
+  uint16_t* planeB = planeA + (size_t)S * KG * TCM * 8;
+  TcShared& sh = *reinterpret_cast<TcShared*>(smem_raw + planes_bytes<S>());
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = (int)(blockIdx.x % ntiles);
+  const int64_t row0 = (int64_t)(blockIdx.x / ntiles) * TCM;
+  const int tn = tile * TCN;
+  const int nq = min(TCN, m - tn);
+  const int Nmma = (nq + 15) / 16 * 16;
+  const int nchunks = (s + TCK - 1) / TCK;
+
+  if (tid == 0) sh.segU = Sg;
+  for (int i = tid; i < TCM; i += kThr) sh.rA[i] = kNone;
+  for (int i = tid; i < TCN; i += kThr) sh.rB[i] = kNone;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sh.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = sh.tmem_base;
+  const uint32_t acc2 = tmem, acc3 = tmem + TCN, accl = tmem + 2 * TCN;
+  const int my_row = 32 * (warp & 3) + lane;
+  const int col0 = 72 * (warp >> 2);
+  float hi[72], lo[72];
+#pragma unroll
+  for (int j = 0; j < 72; ++j) hi[j] = lo[j] = 0.f;
+  uint32_t phase = 0;
+  bool failed = false;
+  const uint32_t idesc = instr_desc(TCM, Nmma);
+  const uint32_t aBase = smem_u32(planeA), bBase = smem_u32(planeB);
+
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int k0 = ch * TCK;
+    // ---- row exponents of the balanced S chunk (items: row x 8 consecutive k)
+    for (int it = tid; it < KG * TCM; it += kThr) {
+      const int rl = it % TCM, kg = it / TCM;
+      const int64_t row = row0 + rl;
+      int e = kZero;
+      if (row < n) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = k0 + kg * 8 + i;
+          if (k < s) {
+            int64_t ld;
+            const double* col = seg_col(sh.segU, k, &ld);
+            const double x = col[row * ld];
+            const int ee = eff_exp0(x);
+            if (ee != kZero) e = max(e, ee - (colexp ? colexp[k] : 0));
+          }
+        }
+      }
+      sh.emA[kg][rl] = e;
+    }
+    // ---- B planes and exponents of this chunk / column tile (pre-split)
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(
+          Cs + (size_t)(ch * ntiles + tile) * S * KG * (TCN / 8) * 64);
+      uint4* dst = reinterpret_cast<uint4*>(planeB);
+      const int nvec = S * KG * (TCN / 8) * 64 / 8;
+      for (int v = tid; v < nvec; v += kThr) dst[v] = src[v];
+      for (int j = tid; j < TCN; j += kThr) sh.eB[j] = Ce[(ch * ntiles + tile) * TCN + j];
+    }
+    __syncthreads();
+    if (tid == 0) sh.rescale = 0;
+    __syncthreads();
+    for (int c = tid; c < TCM + TCN; c += kThr) {
+      if (c < TCM) {
+        int e = kZero;
+        for (int kg = 0; kg < KG; ++kg) e = max(e, sh.emA[kg][c]);
+        const int E = e - 1022;
+        const int rn = max(sh.rA[c], E - kWindow);
+        sh.dA[c] = (sh.rA[c] == kNone) ? 0 : sh.rA[c] - rn;
+        if (sh.dA[c] != 0) sh.rescale = 1;
+        sh.rA[c] = rn;
+        sh.eA[c] = E;
+      } else {
+        const int j = c - TCM;
+        const int E = sh.eB[j];
+        const int rn = max(sh.rB[j], E - kWindow);
+        sh.dB[j] = (sh.rB[j] == kNone) ? 0 : sh.rB[j] - rn;
+        if (sh.dB[j] != 0) sh.rescale = 1;
+        sh.rB[j] = rn;
+        sh.sB[j] = p2f(E - rn);
+      }
+    }
+    __syncthreads();
+    // ---- split the S chunk into the A planes
+    for (int it = tid; it < KG * TCM; it += kThr) {
+      const int rl = it % TCM, kg = it / TCM;
+      const int64_t row = row0 + rl;
+      const int E = sh.eA[rl];
+      uint32_t w[S][4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = k0 + kg * 8 + i;
+        double x = 0.0;
+        int cs = 0;
+        if (row < n && k < s) {
+          int64_t ld;
+          const double* col = seg_col(sh.segU, k, &ld);
+          x = col[row * ld];
+          cs = colexp ? colexp[k] : 0;
+        }
+        uint16_t dg[S];
+        split_weighted<S>(x, E + cs, dg);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+          if (i & 1)
+            w[sl][i >> 1] |= (uint32_t)dg[sl] << 16;
+          else
+            w[sl][i >> 1] = dg[sl];
+        }
+      }
+      uint16_t* dst = planeA + ((size_t)(kg * (TCM / 8) + (rl >> 3)) * 64 + (rl & 7) * 8);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+        *reinterpret_cast<uint4*>(dst + (size_t)sl * KG * (TCM / 8) * 64) =
+            make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n");
+    __syncthreads();
+    if (tc_mma_and_flush<S>(sh, tid, warp, lane, my_row, col0, aBase, bBase, idesc, acc2, acc3,
+                            accl, phase, hi, lo)) {
+      failed = true;
+      break;
+    }
+  }
+  // ---- output rows: Y = (hi + lo) 2^(rA + rB) + beta Y0
+  const int64_t row = row0 + my_row;
+  if (row < n) {
+#pragma unroll
+    for (int j = 0; j < 72; ++j) {
+      const int c = tn + col0 + j;
+      if (col0 + j < nq) {
+        const double y0 = beta != 0.0 ? seg_load(Y0, c, row) : 0.0;
+        *out_addr(Y, c, row) =
+            failed ? __longlong_as_double(0x7FF8000000000000LL)
+                   : assemble_df(hi[j], lo[j], sh.rA[my_row] + sh.rB[col0 + j], y0);
       }
     }
   }
@@ -499,6 +717,76 @@ int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, doub
   }
   if (rc) return rc;
   return ozaki_slab_reduce(st, partial, slabs, p, q, G, ldg);
+}
+
+}  // namespace lob
+
+namespace lob {
+
+namespace {
+
+template <int S>
+int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const double* C,
+                     int64_t ldc, int m, double alpha, double beta, const SegList& Y0,
+                     const OutList& Y, const int* colexp, void* work) {
+  const int ntiles = (int)ceil_div(m, TCN);
+  const int nchunks = (int)ceil_div(s, TCK);
+  uint16_t* Cs = (uint16_t*)work;
+  const size_t cs_elems = (size_t)nchunks * ntiles * S * KG * (TCN / 8) * 64;
+  int* Ce = (int*)(Cs + cs_elems);
+  int* cx = Ce + (size_t)nchunks * ntiles * TCN;
+  if (!colexp) {
+    int rc = column_exponents(st, n, Sg, s, cx);
+    if (rc) return rc;
+    colexp = cx;
+  }
+  {
+    const int64_t warps = (int64_t)nchunks * ntiles * TCN;
+    split_c_tc_kernel<S><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
+        C, ldc, s, m, ntiles, alpha, colexp, Cs, Ce);
+    LOB_LAUNCHED();
+  }
+  const size_t sh = tc_smem_bytes<S>();
+  static bool configured = false;
+  if (!configured) {
+    LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    configured = true;
+  }
+  const int64_t blocks = ceil_div(n, TCM) * ntiles;
+  ozaki_update_tc_kernel<S><<<(unsigned)blocks, kThr, sh, st>>>(n, Sg, s, colexp, Cs, Ce, m,
+                                                                ntiles, beta, Y0, Y);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
+}  // namespace
+
+int64_t update_tc_workspace(int64_t, int s, int m, int slices) {
+  if (slices == 0) slices = 6;
+  const int64_t ntiles = ceil_div(std::max(m, 1), TCN);
+  const int64_t nchunks = ceil_div(std::max(s, 1), TCK);
+  return nchunks * ntiles * slices * KG * (TCN / 8) * 64 * 2 + nchunks * ntiles * TCN * 4 +
+         (int64_t)std::max(s, 1) * 4 + 256;
+}
+
+int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc, int m,
+              double alpha, double beta, const SegList& Y0, const OutList& Y, int slices,
+              void* work, int64_t work_bytes, const int* colexp) {
+  const int s = S.off[S.nseg];
+  if (n <= 0 || m <= 0) return LOBPCG_OK;
+  if (slices == 0) slices = 6;
+  if (s == 0) return update_f64(st, n, S, C, ldc, m, alpha, beta, Y0, Y);
+  if (work_bytes < update_tc_workspace(n, s, m, slices)) return LOBPCG_ERR_ARG;
+  if (beta != 0.0 && beta != 1.0) return LOBPCG_ERR_ARG;
+  switch (slices) {
+    case 3: return update_tc_launch<3>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    case 4: return update_tc_launch<4>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    case 5: return update_tc_launch<5>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    case 6: return update_tc_launch<6>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    case 7: return update_tc_launch<7>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    default: return LOBPCG_ERR_ARG;
+  }
 }
 
 }  // namespace lob

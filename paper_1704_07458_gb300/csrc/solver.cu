@@ -207,6 +207,9 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   h->gwork_bytes = gb;
   if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
   h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)) : 0;
+  if (mode == LOBPCG_GEMM_OZAKI_TC)
+    h->uwork_bytes = std::max(h->uwork_bytes,
+                              update_tc_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)));
   if (h->uwork_bytes > 0 && (rc = dalloc(h, &h->uwork, (size_t)h->uwork_bytes))) return rc;
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
@@ -244,6 +247,9 @@ int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m,
            int min_slices = 0) {
   h->stats.update_calls++;
   h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
+  if (gemm_mode(h) == LOBPCG_GEMM_OZAKI_TC)
+    return update_tc(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
+                     std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);
   if (gemm_mode(h))
     return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
                         std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);
