@@ -160,7 +160,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="f64", choices=["f64", "ozaki"])
+    ap.add_argument("--mode", default="ozaki_tc", choices=["f64", "ozaki", "ozaki_tc"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--ref-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -252,11 +252,15 @@ def main():
         e2e_s = float(t.item())
 
     # ---- roofline of the dominant n-scaled kernel over the timed region
+    # FP64 mode: FP64 flops on the CUDA cores ("alu"); emulated modes: the BF16
+    # tensor-core flops of the digit products ("tensor").
+    f64 = args.mode == "f64"
     phases = {
         "spmm": (tot["ms_spmm"], tot["spmm_bytes"], "hbm"),
-        "gram": (tot["ms_gram"], tot["gram_flops"], "alu" if args.mode == "f64" else "tensor"),
-        "update": (tot["ms_update"], tot["update_flops"],
-                   "alu" if args.mode == "f64" else "tensor"),
+        "gram": (tot["ms_gram"], tot["gram_flops"] if f64 else tot["gram_tensor_flops"],
+                 "alu" if f64 else "tensor"),
+        "update": (tot["ms_update"], tot["update_flops"] if f64 else tot["update_tensor_flops"],
+                   "alu" if f64 else "tensor"),
     }
     dom = max(phases, key=lambda k: phases[k][0])
     t_ms, work, bound = phases[dom]
@@ -275,8 +279,12 @@ def main():
     per_phase = {k: {"ms_per_solve": v[0] / args.steps,
                      "rate": (v[1] / (v[0] * 1e-3) / (1e9 if v[2] == "hbm" else 1e12))
                      if v[0] > 0 else None,
-                     "unit": "GB/s" if v[2] == "hbm" else "TFLOP/s (FP64-equivalent)"}
+                     "unit": {"hbm": "GB/s", "alu": "FP64 TFLOP/s",
+                              "tensor": "BF16 TFLOP/s"}[v[2]]}
                  for k, v in phases.items()}
+    for k, key in (("gram", "gram_flops"), ("update", "update_flops")):
+        t = phases[k][0]
+        per_phase[k]["fp64_equivalent_tflops"] = tot[key] / (t * 1e-3) / 1e12 if t > 0 else None
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "traffic": None,
                 "peak_source": peak_src, "phases": per_phase}

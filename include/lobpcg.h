@@ -92,6 +92,9 @@ typedef struct {
    * for a fused diagonal B]; Gram flops 2 n p q; update flops 2 n s m. */
   int64_t spmm_calls, gram_calls, update_calls;
   double spmm_bytes, gram_flops, update_flops;
+  /* BF16 tensor-core work of the emulated contractions: the FP64-equivalent
+   * flops times the S(S+1)/2 digit pairs of an S-slice split (0 in FP64 mode) */
+  double gram_tensor_flops, update_tensor_flops;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.

@@ -76,6 +76,8 @@ class lobpcg_stats_t(ctypes.Structure):
         ("spmm_bytes", ctypes.c_double),
         ("gram_flops", ctypes.c_double),
         ("update_flops", ctypes.c_double),
+        ("gram_tensor_flops", ctypes.c_double),
+        ("update_tensor_flops", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -208,8 +208,9 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
   h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)) : 0;
   if (mode == LOBPCG_GEMM_OZAKI_TC)
-    h->uwork_bytes = std::max(h->uwork_bytes,
-                              update_tc_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)));
+    h->uwork_bytes = std::max({h->uwork_bytes,
+                               update_tc_workspace(n, (int)nsmax, (int)(2 * nx), sl),
+                               update_tc_workspace(n, (int)nsmax, (int)(2 * nx), 7)});
   if (h->uwork_bytes > 0 && (rc = dalloc(h, &h->uwork, (size_t)h->uwork_bytes))) return rc;
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
@@ -231,6 +232,10 @@ int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t l
          int min_slices = 0) {
   h->stats.gram_calls++;
   h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
+  if (gemm_mode(h)) {
+    const int sl = std::max(slices(h), min_slices);
+    h->stats.gram_tensor_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg] * sl * (sl + 1) / 2;
+  }
   if (gemm_mode(h) == LOBPCG_GEMM_OZAKI_TC)
     return gram_tc(h->st, h->n, U, V, G, ldg, std::max(slices(h), min_slices), h->gwork,
                    h->gwork_bytes);
@@ -247,6 +252,10 @@ int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m,
            int min_slices = 0) {
   h->stats.update_calls++;
   h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
+  if (gemm_mode(h)) {
+    const int sl = std::max(slices(h), min_slices);
+    h->stats.update_tensor_flops += 2.0 * h->n * S.off[S.nseg] * m * sl * (sl + 1) / 2;
+  }
   if (gemm_mode(h) == LOBPCG_GEMM_OZAKI_TC)
     return update_tc(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
                      std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);

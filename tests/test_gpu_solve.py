@@ -103,13 +103,26 @@ def test_c2_reduced_oracle_parity(mode):
     _check_pairs(p, lam, X, be, r.normA, r.normB)
 
 
-def test_forced_orthogonalisation_path():
+@pytest.mark.parametrize("mode", MODES)
+def test_forced_orthogonalisation_path(mode):
+    """tau_skip = 1: Algorithm 5 (7-slice Grams and updates) from iteration 1."""
     p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
-    lam, X, it, be, rc, st = _gpu(p, tau_skip=1.0)
+    lam, X, it, be, rc, st = _gpu(p, mode=mode, tau_skip=1.0)
     assert rc == 0 and st["flip_iteration"] == 1 and st["ortho_calls"] >= it
     _, r = _oracle(p, opts=L.Options(tau_skip=1.0))
     np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
     _check_pairs(p, lam, X, be, r.normA, r.normB)
+    # Algorithm 5 rarely needs more than two svqb passes per call here
+    assert st["svqb_passes"] <= 4 * st["ortho_calls"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_forced_orthogonalisation_larger(mode):
+    """Orthogonal branch on a 16^3 pencil with 40 pairs (ortho Grams over many chunks)."""
+    p = synth.make_problem("lap3d_64_diagB", N=16, k=40)
+    lam, X, it, be, rc, st = _gpu(p, mode=mode, tau_skip=1.0)
+    assert rc == 0
+    _check_pairs(p, lam, X, be, st["norm_a"], st["norm_b"], tol_orth=1e-11)
 
 
 def test_periodic_singular_hamiltonian():
