@@ -188,13 +188,18 @@ def main():
 
     solver = gb.Solver(stream=stream, gemm_mode=args.mode)
     solver.set_operator(A_rp, A_ci, A_v, b_diag=bd)
+    # the seeded starting block, resident in HBM like the operator; the e2e leg
+    # below copies the same block from pinned host memory
+    nx = synth.block_width(p.k)
+    X0h = torch.from_numpy(synth.normal_block(seed, synth.STREAM_X0, p.n, nx)).pin_memory()
+    X0d = X0h.cuda()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     for _ in range(args.warmup):
-        lam, X, it, be, rc = solver.solve(p.k, p.tol, seed=seed, device=True)
+        lam, X, it, be, rc = solver.solve(p.k, p.tol, X0=X0d, seed=seed, device=True)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -204,7 +209,7 @@ def main():
     tot = {}
     e0.record(stream)
     for _ in range(args.steps):
-        lam, X, it, be, rc = solver.solve(p.k, p.tol, seed=seed, device=True)
+        lam, X, it, be, rc = solver.solve(p.k, p.tol, X0=X0d, seed=seed, device=True)
         st = solver.stats()
         for key, v in st.items():
             tot[key] = tot.get(key, 0) + v
@@ -221,8 +226,6 @@ def main():
     bemax = float(be.max().item())
 
     # ---- end to end through the C ABI with host buffers
-    nx = synth.block_width(p.k)
-    X0h = torch.from_numpy(synth.normal_block(seed, synth.STREAM_X0, p.n, nx)).pin_memory()
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_rp, h_ci, h_v = pin(p.A.rowptr), pin(p.A.col), pin(p.A.val)
     h_b = pin(p.b_diag) if p.b_diag is not None else None
@@ -241,7 +244,7 @@ def main():
         rc_e = gb.lobpcg_set_operator(e2e_solver.h, p.n, h_rp, h_ci, h_v, p.A.nnz, B_diag=h_b,
                                       mem=gb.LOBPCG_MEM_HOST)
         assert rc_e == 0
-        rc_e, _ = gb.lobpcg_solve(e2e_solver.h, p.k, p.tol, X0h, nx, seed, gb.LOBPCG_MEM_HOST,
+        rc_e, it_e = gb.lobpcg_solve(e2e_solver.h, p.k, p.tol, X0h, nx, seed, gb.LOBPCG_MEM_HOST,
                                   lam_h, X_h, p.k, gb.LOBPCG_MEM_HOST, be_h)
         assert rc_e == 0, rc_e
     torch.cuda.synchronize()
@@ -296,11 +299,19 @@ def main():
         "dtype": "f64", "data": "synthetic", "config": workload_config(args, p),
         "iterations": int(it), "max_backward_error": bemax,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "iterations": int(it_e)},
         "gpu_launches": int(tot["gpu_launches"]),
         "clocks": clk, "roofline": roofline,
-        "small_dense_ms_per_solve": tot["ms_small_dense"] / args.steps,
-        "residual_ms_per_solve": tot["ms_residual"] / args.steps,
+        # per-solve phase times (CUDA events on the solver's stream, exclusive:
+        # they add up to the stream time; "total" is the host wall clock)
+        "phases_ms_per_solve": {
+            k[3:]: tot[k] / args.steps for k in
+            ("ms_spmm", "ms_gram", "ms_update", "ms_residual", "ms_small_dense", "ms_ortho",
+             "ms_other", "ms_total")},
+        "solver": {"flip_iteration": int(st["flip_iteration"]),
+                   "ortho_calls": int(st["ortho_calls"]), "svqb_passes": int(st["svqb_passes"]),
+                   "dropped_columns": int(st["dropped_columns"]),
+                   "launches_per_solve": int(tot["gpu_launches"]) // max(1, args.steps)},
     }
     line["config"]["block_width"] = int(st["n_x"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -84,9 +84,14 @@ typedef struct {
   int64_t gpu_launches;   /* kernels of this library launched by the last solve */
   double norm_a, norm_b;  /* Gaussian-sketch norm estimates used in Eq. (9) */
   double max_backward_error;
-  /* phase times in ms from CUDA events on the handle's stream; a phase includes
-   * the phases nested in it (ms_ortho contains its Gram, update and B products) */
-  double ms_spmm, ms_gram, ms_update, ms_residual, ms_small_dense, ms_ortho, ms_total;
+  /* phase times in ms from CUDA events on the handle's stream, exclusive: time
+   * inside a phase nested in another is charged to the inner one only (the
+   * Grams of orthoDrop count as ms_gram, its own small kernels and host waits
+   * as ms_ortho); ms_other is the stream time of the solve outside every phase
+   * (norm sums, exponent kernels, host decisions between phases), so the six
+   * phases and ms_other add up to the solve's stream time.  ms_total: host
+   * wall-clock time of lobpcg_solve. */
+  double ms_spmm, ms_gram, ms_update, ms_residual, ms_small_dense, ms_ortho, ms_other, ms_total;
   /* algorithmic work of the n-scaled kernels over the solve (for roofline figures):
    * SpMM bytes nnz*(8+4) + 4(n+1) + 8 n m (X read) + 8 n m (Y written) [+ 8 n + 16 n m
    * for a fused diagonal B]; Gram flops 2 n p q; update flops 2 n s m. */

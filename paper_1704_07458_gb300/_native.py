@@ -69,6 +69,7 @@ class lobpcg_stats_t(ctypes.Structure):
         ("ms_residual", ctypes.c_double),
         ("ms_small_dense", ctypes.c_double),
         ("ms_ortho", ctypes.c_double),
+        ("ms_other", ctypes.c_double),
         ("ms_total", ctypes.c_double),
         ("spmm_calls", ctypes.c_int64),
         ("gram_calls", ctypes.c_int64),

@@ -28,14 +28,18 @@ using namespace lob;
 namespace {
 constexpr double kEps = 2.220446049250313e-16;
 
-enum Phase { PH_SPMM, PH_GRAM, PH_UPDATE, PH_RESID, PH_DENSE, PH_ORTHO, PH_COUNT };
+enum Phase { PH_SPMM, PH_GRAM, PH_UPDATE, PH_RESID, PH_DENSE, PH_ORTHO, PH_OTHER, PH_COUNT };
 
 struct PhaseTimer {
-  // Nesting-safe: a phase's time includes the phases opened inside it.
+  // Exclusive accounting on the stream: every phase boundary records an event
+  // and the interval since the previous boundary is charged to the innermost
+  // open phase, or to PH_OTHER when no phase is open.  The totals therefore
+  // add up to the stream time between the first and the last boundary.
   std::vector<cudaEvent_t> pool;
-  struct Mark { int phase; int e0, e1; };
-  std::vector<Mark> marks;
-  std::vector<std::pair<int, int>> open;  // (phase, start event) stack
+  struct Seg { int phase; int e0, e1; };
+  std::vector<Seg> segs;
+  std::vector<int> open;  // phase stack
+  int last = -1;          // event of the previous boundary
   size_t used = 0;
   double total[PH_COUNT] = {0};
   cudaStream_t st = nullptr;
@@ -48,24 +52,38 @@ struct PhaseTimer {
     cudaEventRecord(pool[used], st);
     return (int)used++;
   }
-  void begin(int ph) { open.push_back({ph, ev()}); }
-  void end() {
-    const auto top = open.back();
-    open.pop_back();
-    marks.push_back({top.first, top.second, ev()});
+  void mark() {
+    const int e = ev();
+    if (last >= 0) segs.push_back({open.empty() ? PH_OTHER : open.back(), last, e});
+    last = e;
   }
-  // Call only after a stream synchronisation with no phase open.
+  void begin(int ph) {
+    mark();
+    open.push_back(ph);
+  }
+  void end() {
+    mark();
+    open.pop_back();
+  }
+  // Call only after a stream synchronisation.
   void flush() {
-    for (auto& m : marks) {
+    for (auto& m : segs) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, pool[m.e0], pool[m.e1]) == cudaSuccess) total[m.phase] += ms;
     }
-    marks.clear();
-    if (open.empty()) used = 0;
+    segs.clear();
+    if (last >= 0) {  // keep only the last boundary's event
+      std::swap(pool[0], pool[last]);
+      last = 0;
+      used = 1;
+    } else {
+      used = 0;
+    }
   }
   void reset() {
-    flush();
+    segs.clear();
     open.clear();
+    last = -1;
     used = 0;
     for (auto& t : total) t = 0;
   }
@@ -230,6 +248,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
 // does not.
 int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t ldg,
          int min_slices = 0) {
+  Scoped sc(h->timer, PH_GRAM);
   h->stats.gram_calls++;
   h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
   if (gemm_mode(h)) {
@@ -250,6 +269,7 @@ int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t l
 int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m, double alpha,
            double beta, const SegList& Y0, const OutList& Y, const int* colexp,
            int min_slices = 0) {
+  Scoped sc(h->timer, PH_UPDATE);
   h->stats.update_calls++;
   h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
   if (gemm_mode(h)) {
@@ -425,6 +445,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   const int64_t launches0 = g_launches;
   h->timer.st = h->st;
   h->timer.reset();
+  h->timer.mark();
   h->stats = lobpcg_stats_t{};
   h->stats.n_x = nx;
   h->stats.flip_iteration = -1;
@@ -675,6 +696,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
                                 k * sizeof(double), n, kind, h->st));
   LOB_CUDA_OK(cudaMemcpyAsync(lambda, h->theta, k * sizeof(double), kind, h->st));
   if (resnorm) LOB_CUDA_OK(cudaMemcpyAsync(resnorm, h->be, k * sizeof(double), kind, h->st));
+  h->timer.mark();
   if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
   LOB_CUDA_OK(cudaStreamSynchronize(h->st));
   h->timer.flush();
@@ -690,6 +712,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.ms_residual = h->timer.total[PH_RESID];
   h->stats.ms_small_dense = h->timer.total[PH_DENSE];
   h->stats.ms_ortho = h->timer.total[PH_ORTHO];
+  h->stats.ms_other = h->timer.total[PH_OTHER];
   h->stats.ms_total =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (iters) *iters = it;
