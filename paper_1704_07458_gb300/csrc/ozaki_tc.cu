@@ -1,28 +1,35 @@
-// Tensor-core (tcgen05 / TMEM) version of the Ozaki-split Gram G = U^T V.
+// Tensor-core (tcgen05 / TMEM) FP64 emulation of the two n-scaled
+// contractions of an LOBPCG iteration (Sec. 5.2, Eqs. (10)-(14)): the Gram
+// G = U^T V and the basis update Y = beta Y0 + alpha S C.
 //
-// Same arithmetic contract as ozaki.cu (exact BF16 digit products, FP64-class
-// result, no FP64 instruction on the hot path), mapped onto the sm_100-family
-// tensor cores:
+// Arithmetic (the contract of ozaki.cu): each FP64 operand is cut, relative to
+// an exponent shared by a block of values, into S signed 8-bit digits (exact
+// in BF16); digit products are exact; every level of digit pairs but the last
+// is summed exactly in an FP32 TMEM accumulator; accumulators are converted
+// exactly into int64 registers and the FP64 result is assembled with integer
+// operations only.  No FP64 instruction runs on the hot path.
 //
-//  * one CTA owns a 128 x 144 output tile (128 columns of U = MMA M, up to 144
-//    columns of V = MMA N) and a slab of rows; the contraction runs in chunks
-//    of 32 rows;
-//  * staging: every thread loads FP64 values of the chunk, the chunk column
-//    exponents E are reduced in shared memory, and each value is cut into S
-//    signed 8-bit digits d_s; plane s stores d_s * 2^(-8(s-1)) (exact BF16) in
-//    the K-major, no-swizzle core-matrix layout of the UMMA shared-memory
-//    descriptors (8 rows x 16 bytes per core matrix), written as 16-byte stores;
-//  * one elected thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32)
-//    into three TMEM accumulators: level 2 (digit pair (1,1)), level 3 (pairs
-//    (1,2), (2,1)) and all pairs of levels 4 .. S+1.  With |d| <= 128 and 32
-//    rows per chunk the first two are exact; the third holds terms below 2^-16
-//    of the first, so its FP32 rounding contributes < 2^-40;
-//  * completion is signalled through tcgen05.commit on an mbarrier; the wait is
-//    bounded (a missed completion marks the result NaN instead of hanging);
-//  * flush: each thread reads its TMEM lane (one output row) with tcgen05.ld
-//    and adds the three scaled sums into a double-float (two FP32) register
-//    accumulator relative to per-column reference exponents;
-//  * the slab partials (hi, lo, exponent) go through ozaki_slab_reduce_kernel.
+// GB300 mapping:
+//  * one CTA (256 threads, one CTA per SM) owns a 128 x NT output tile,
+//    NT <= 96 a multiple of 16: tcgen05.mma kind::f16, M = 128, N = NT, K = 16;
+//  * the contraction runs in chunks of 16 (rows of U and V for the Gram,
+//    columns of S for the update), grouped in blocks of 256 that share one
+//    exponent per operand column (Gram) or row (update).  With |digit| <= 128
+//    the sums of levels 0, 1, 2 (and 3 for S = 7) stay below 2^24 in their
+//    units over a block, so they are exact in FP32; the deeper levels (below
+//    2^-24 resp. 2^-32 of level 0) share one inexact accumulator.  4 or 5
+//    accumulators x NT columns fit the 512 TMEM columns, and TMEM is read once
+//    per block instead of once per chunk;
+//  * the raw FP64 operands stream into three shared-memory stages by cp.async,
+//    two chunks ahead of use, so that no thread waits on a global load; the
+//    digit planes have two stages: the tensor core multiplies chunk c while
+//    the 256 threads cut chunk c + 1; the digits of the small matrix C of the
+//    update are cut once per call and arrive by cp.async.bulk;
+//  * the shared exponents come from a streaming pre-pass at full occupancy
+//    (per 256-row block and column for the Gram, per row for the update), so
+//    the tensor-core kernels never wait on a global load of their own;
+//  * every mbarrier wait is bounded: a wait that runs out marks the result NaN
+//    and the CTA returns instead of hanging.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -31,69 +38,95 @@
 namespace lob {
 namespace {
 
-constexpr int TCM = 128;        // MMA M: columns of U per tile
-constexpr int TCN = 144;        // max MMA N: columns of V per tile
-constexpr int TCK = 32;         // rows per chunk
-constexpr int KG = TCK / 8;     // core-matrix groups along K
+constexpr int TCM = 128;            // MMA M
+constexpr int TCK = 16;             // contraction length of a chunk (one MMA K)
+constexpr int KG = TCK / 8;         // core-matrix groups along K in a chunk
+constexpr int kChunksPerBlock = 16; // 256 rows / columns share one exponent
+constexpr int kRaw = 3;             // raw FP64 stages (prefetch distance 2)
+constexpr int kBlock = TCK * kChunksPerBlock;
+constexpr int NTMAX = 96;           // max MMA N (output columns of a tile)
 constexpr int kThr = 256;
-constexpr int kZero = -30000;
-constexpr int kNone = -100000;
-constexpr int kWindow = 40;     // reference exponent = chunk max - kWindow (lazy)
+constexpr int kFrac = 30;           // fraction bits of the int64 accumulators
+constexpr int kEZero = -4000;       // exponent of an all-zero block
 constexpr uint32_t kTmemCols = 512;
+constexpr int kSpin = 1 << 22;      // bound of every mbarrier wait
+constexpr int kMaxUpdateK = 6144;   // columns of S an update takes (3 n_x <= 6144)
 
-__device__ __forceinline__ int eff_exp0(double x) {
-  const long long b = __double_as_longlong(x);
-  if ((b & 0x7FFFFFFFFFFFFFFFLL) == 0) return kZero;
-  const int be = (int)((b >> 52) & 0x7FF);
-  return be == 0 ? 1 : be;
-}
-
-__device__ __forceinline__ float p2f(int k) {
-  return k < -126 ? 0.0f : (k > 127 ? __int_as_float(0x7F000000) : __int_as_float((k + 127) << 23));
-}
-
-// S pre-weighted digits of x relative to 2^E (biased-exponent bound eb = E + 1022),
-// as BF16 bit patterns: plane s holds d_s * 2^(-8 s) (s = 0 .. S-1).
 template <int S>
-__device__ __forceinline__ void split_weighted(double x, int E, uint16_t out[S]) {
-  const long long bits = __double_as_longlong(x);
-  const int be = (int)((bits >> 52) & 0x7FF);
-  long long mant = bits & 0x000FFFFFFFFFFFFFLL;
-  if (be != 0) mant |= 0x0010000000000000LL;
-  const int sh = (be == 0 ? 1 : be) - 1076 + 8 * S - E;
-  long long F;
-  if (mant == 0 || sh <= -64) {
-    F = 0;
-  } else if (sh >= 0) {
-    F = mant << sh;
-  } else {
-    F = (mant + (1LL << (-sh - 1))) >> (-sh);
-  }
-  if (bits < 0) F = -F;
-  int d[S];
-#pragma unroll
-  for (int s = S - 1; s >= 1; --s) {
-    const int v = (int)((F & 0xFF) ^ 0x80) - 0x80;
-    F = (F - v) >> 8;
-    d[s] = v;
-  }
-  d[0] = (int)F;
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const float f = (__int_as_float(0x4B400000 + d[s]) - 12582912.0f) * p2f(-8 * s);
-    out[s] = (uint16_t)(__float_as_uint(f) >> 16);
-  }
-}
+__host__ __device__ constexpr int nacc() { return S >= 7 ? 5 : (S < 4 ? S : 4); }
+// accumulator of digit level l = s + t (0-based digit indices)
+template <int S>
+__host__ __device__ constexpr int acc_of(int l) { return l < nacc<S>() - 1 ? l : nacc<S>() - 1; }
+template <int S>
+__host__ __device__ constexpr size_t planeA_bytes() { return (size_t)KG * (TCM / 8) * 128; }
+__host__ __device__ inline size_t planeB_bytes(int NT) { return (size_t)KG * (NT / 8) * 128; }
 
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  lo += (hi - (s - bb)) + (v - bb);
-  hi = s;
+// 0x80 in each of the S-1 low bytes: adding it turns the fixed-point value
+// into bytes that are the balanced digits plus 128.
+template <int S>
+__host__ __device__ constexpr long long digit_bias() {
+  long long b = 0;
+  for (int i = 0; i < S - 1; ++i) b |= 0x80LL << (8 * i);
+  return b;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Digits of x relative to the exponent bound E (|x| < 2^E): the fixed-point
+// integer F = round(x 2^(8S-1-E)) (|F| <= 2^(8S-1)) written in balanced base
+// 256, F = sum_s d_s 256^(S-1-s), |d_s| <= 128; returns the pre-weighted
+// values d_s 2^(-8s), each exact in BF16.  Integer operations only.
+template <int S>
+__device__ __forceinline__ void digits(double x, int E, float (&d)[S]) {
+  const long long bits = __double_as_longlong(x);
+  const int be = (int)((bits >> 52) & 0x7FF);
+  long long mant = bits & 0x000FFFFFFFFFFFFFLL;
+  if (be != 0) mant |= 0x0010000000000000LL;
+  const int sh = max(be, 1) - 1076 + 8 * S - E;
+  long long F;
+  if (sh >= 0) {
+    F = mant << min(sh, 10);  // sh <= 2 whenever |x| < 2^E
+  } else {
+    const int r = -sh;
+    F = r > 62 ? 0 : ((mant >> (r - 1)) + 1) >> 1;
+  }
+  if (bits < 0) F = -F;
+  const long long G = F + digit_bias<S>();
+  const uint32_t lo = (uint32_t)G, hi = (uint32_t)((unsigned long long)G >> 32);
+#pragma unroll
+  for (int s = 1; s < S; ++s) {
+    const int b = S - 1 - s;  // byte of digit s
+    const uint32_t w = b < 4 ? lo : hi;
+    // 0x4B0000xx is 2^23 + xx; minus (2^23 + 128), scaled by 2^-8s (exact)
+    const float f = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(b & 3)));
+    const float sc = __uint_as_float((uint32_t)(127 - 8 * s) << 23);
+    d[s] = fmaf(f, sc, -8388736.0f * sc);
+  }
+  d[0] = (float)(int)(G >> (8 * (S - 1)));
+}
+
+// 8 consecutive K values of one M/N index -> S planes, one 16-byte shared
+// store per plane (K-major core-matrix row: 8 BF16 along K).
+template <int S>
+__device__ __forceinline__ void split8(const double (&x)[8], const int (&E)[8], uint32_t dst,
+                                       uint32_t pstride) {
+  uint32_t w[S][4];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    float a[S], b[S];
+    digits<S>(x[i], E[i], a);
+    digits<S>(x[i + 1], E[i + 1], b);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      w[s][i >> 1] = __byte_perm(__float_as_uint(a[s]), __float_as_uint(b[s]), 0x7632);
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(dst + s * pstride),
+                 "r"(w[s][0]), "r"(w[s][1]), "r"(w[s][2]), "r"(w[s][3])
+                 : "memory");
 }
 
 // UMMA shared-memory descriptor: K-major, no swizzle.  lbo: byte distance of
@@ -113,8 +146,8 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                            uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
@@ -132,556 +165,914 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-struct TcShared {
-  // digit planes: [S][KG][TCM/8][8 rows][8 bf16] for A, [S][KG][TCN/8][8][8] for B
-  // (sized for the largest S at run time; see tc_stage_bytes)
-  int eA[TCM], eB[TCN];        // chunk exponent bound E per column
-  int rA[TCM], rB[TCN];        // reference exponents
-  int dA[TCM], dB[TCN];        // reference change of this chunk (<= 0)
-  int emA[KG][TCM], emB[KG][TCN];
-  float sB[TCN];               // per-column chunk scale 2^(eB - rB)
-  SegList segU, segV;
-  unsigned long long mbar;
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count));
+}
+
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  uint32_t done = 0;
+  for (int spin = 0; spin < kSpin && !done; ++spin)
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                   dst_smem),
+               "r"(kTmemCols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t tmem) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+               "r"(kTmemCols));
+}
+
+// All digit-pair MMAs of one chunk (both K halves) into the accumulators.
+// started: bit a set once accumulator a has been written in this block.
+// (TCK = 16: one MMA of K = 16 per digit pair.)  The descriptors of the
+// planes differ from the stage's first one only in the 14-bit start address
+// field (shared addresses < 256 KB), so they are formed by addition.
+template <int S>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, int NT, uint32_t aStage,
+                                            uint32_t bStage, uint32_t& started) {
+  static_assert(TCK == 16, "one MMA per digit pair and chunk");
+  const uint32_t lboA = (TCM / 8) * 128, lboB = (uint32_t)(NT / 8) * 128, sbo = 128;
+  const uint64_t pa16 = planeA_bytes<S>() >> 4, pb16 = planeB_bytes(NT) >> 4;
+  const uint32_t idesc = instr_desc(TCM, NT);
+  const uint64_t da0 = smem_desc(aStage, lboA, sbo), db0 = smem_desc(bStage, lboB, sbo);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int t = 0; t + s < S; ++t) {
+      const int a = acc_of<S>(s + t);
+      mma_bf16(tmem + (uint32_t)(a * NT), da0 + s * pa16, db0 + t * pb16, idesc,
+               (started >> a) & 1u);
+      started |= 1u << a;
+    }
+}
+
+constexpr int kIssuer = kThr - 32;  // thread that issues MMAs and bulk copies (lightest split load)
+
+// Exact int64 value (units 2^-kFrac of the level-0 unit) of the accumulators
+// of one output: levels 0..2 (and 3 for S = 7) are exact FP32 integers in
+// their units (< 2^24), the last accumulator is rounded at 2^-kFrac.
+template <int S>
+__device__ __forceinline__ long long acc_to_i64(const float (&v)[5]) {
+  constexpr int NA = nacc<S>();
+  long long T = 0;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    // level a in units 2^(-8a); scale so that the int32 conversion is exact
+    // (exact levels) or rounds at 2^-kFrac (last accumulator)
+    const bool last = (a == NA - 1) && (S >= 4);
+    const int sc = last ? kFrac : 8 * a;
+    const int i = __float2int_rn(v[a] * __uint_as_float((uint32_t)(127 + sc) << 23));
+    T += last ? (long long)i : ((long long)i << (kFrac - 8 * a));
+  }
+  return T;
+}
+
+__device__ __forceinline__ long long shr_sat(long long v, int k) {
+  return k <= 0 ? v : (k > 62 ? 0 : (v >> k));
+}
+
+// v * 2^e + y0 rounded to FP64 (error below 1 ulp), integer operations only.
+__device__ __forceinline__ double assemble_i64(long long v, int e, double y0) {
+  if (y0 == 0.0) return int_to_double(v, e);
+  long long my;
+  int ey;
+  double_parts(y0, my, ey);
+  if (v == 0) return y0;
+  const int top = max(e + bitlen(v), ey + bitlen(my));
+  const int base = top - 61;
+  const int kv = e - base, ky = ey - base;
+  const long long a = kv >= 0 ? (v << kv) : shr_sat(v, -kv);
+  const long long b = ky >= 0 ? (my << ky) : shr_sat(my, -ky);
+  return int_to_double(a + b, base);
+}
+
+__device__ __forceinline__ void seg_col_ptr(const SegList& s, int c, const double** p,
+                                            long long* ld) {
+  int i = 0;
+#pragma unroll
+  for (int t = 1; t < kMaxSeg; ++t) i += (t < s.nseg && c >= s.off[t]) ? 1 : 0;
+  *p = s.ptr[i] + (c - s.off[i]);
+  *ld = s.ld[i];
+}
+
+// 8-byte global -> shared copy (zero fill when !valid; src must still be a
+// mapped address), completion tracked by cp.async groups.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const double* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// wait until at most one group of this thread is pending
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait0() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void ld_shared_f64(uint32_t a, double& x) {
+  asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(x) : "r"(a) : "memory");
+}
+
+// ------------------------------------------------------------------- Gram
+constexpr int kGcols = TCM + NTMAX;  // column slots of a Gram tile: A columns, then B columns
+
+struct GramShared {
+  unsigned long long mdone[2];
   uint32_t tmem_base;
-  int rescale;
+  int fail;
+  int eCur[kGcols];   // exponent bounds E of the current block
+  int R[kGcols];      // reference exponents of the int64 accumulators
+  int dR[kGcols];     // reference increase at the current block
+  const double* cptr[kGcols];
+  long long cld[kGcols];
 };
 
 template <int S>
-__host__ __device__ constexpr size_t planes_bytes() {
-  return (size_t)S * KG * (TCM + TCN) * 8 * 2;
+size_t gram_smem_bytes(int NT) {
+  return 2 * (S * planeA_bytes<S>() + S * planeB_bytes(NT)) +
+         (size_t)kRaw * TCK * kGcols * 8 + sizeof(GramShared) + 1024;
 }
 
-__device__ __forceinline__ const double* seg_col(const SegList& s, int c, int64_t* ld) {
-  int i = 0;
-  for (int t = 1; t < s.nseg; ++t) i += (c >= s.off[t]) ? 1 : 0;
-  *ld = s.ld[i];
-  return s.ptr[i] + (c - s.off[i]);
+// E[b][c] = exponent bound of column c over rows [256 b, 256 b + 256): the
+// biased exponent maximum (at least 1) minus 1022.  One warp per (block, 32
+// columns), lanes over columns; high words only.
+__global__ void block_col_exp_kernel(int64_t n, SegList L, int ncols, int64_t nblk,
+                                     int* __restrict__ E) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int c = blockIdx.x * 32 + lane;
+  if (b >= nblk || c >= ncols) return;
+  const double* p;
+  long long ld;
+  seg_col_ptr(L, c, &p, &ld);
+  const int64_t r0 = b * kBlock, r1 = min(n, r0 + kBlock);
+  int e = 1;
+  for (int64_t r = r0; r < r1; r += 16) {
+    int hw[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int64_t row = min(r + i, r1 - 1);
+      hw[i] = __ldg(reinterpret_cast<const int*>(p + row * ld) + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) e = max(e, (hw[i] >> 20) & 0x7FF);
+  }
+  E[b * ncols + c] = e - 1022;
 }
 
-// One core-matrix row: 8 consecutive rows (k) of one column, split into S
-// planes; each plane gets one 16-byte store at dst + s * plane_stride.
-template <int S>
-__device__ __forceinline__ void stage_core(const double* col, int64_t ld, int64_t row0,
-                                           int64_t r1, int E, uint16_t* dst,
-                                           size_t plane_stride) {
-  uint32_t w[S][4];
+// Stage rows [r, r + TCK) of column slot c = tid into raw (row-major
+// [TCK][kGcols]): lanes over consecutive columns (coalesced), rows by pointer
+// increments.
+__device__ __forceinline__ void gram_stage_raw(const GramShared& sh, int ncs, int64_t r,
+                                               int64_t rend, uint32_t raw, int tid,
+                                               const double* any) {
+  if (tid >= ncs) return;
+  const double* p = sh.cptr[tid];
+  const long long ld = sh.cld[tid];
+  const double* src = p ? p + r * ld : any;
+  const int64_t left = rend - r;
+  const int nv = !p ? 0 : (left >= TCK ? TCK : (left > 0 ? (int)left : 0));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t row = row0 + i;
-    const double x = (col && row < r1) ? col[row * ld] : 0.0;
-    uint16_t dg[S];
-    split_weighted<S>(x, E, dg);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      if (i & 1)
-        w[s][i >> 1] |= (uint32_t)dg[s] << 16;
-      else
-        w[s][i >> 1] = dg[s];
-    }
+  for (int i = 0; i < TCK; ++i) {
+    cp_async8(raw + (uint32_t)(i * kGcols + tid) * 8, i < nv ? src : any, i < nv);
+    src += ld;
   }
-#pragma unroll
-  for (int s = 0; s < S; ++s)
-    *reinterpret_cast<uint4*>(dst + s * plane_stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-}
-
-// Phase A (exact levels 2, 3, 4), flush of level 4, phase B (levels 5..S+1 in
-// the same columns), flush of everything into (hi, lo).  The planes of the
-// chunk are in shared memory and fenced.  Returns true if an MMA completion
-// was not observed within the bounded wait.
-template <int S>
-__device__ __forceinline__ bool tc_mma_and_flush(TcShared& sh, int tid, int warp, int lane,
-                                                 int my_row, int col0, uint32_t aBase,
-                                                 uint32_t bBase, uint32_t idesc, uint32_t acc2,
-                                                 uint32_t acc3, uint32_t accl, uint32_t& phase,
-                                                 float (&hi)[72], float (&lo)[72]) {
-  // phase A (one thread): exact levels 2, 3 and 4
-  const uint32_t lboA = (TCM / 8) * 128, lboB = (TCN / 8) * 128, sbo = 128;
-  const uint32_t planeA_bytes = KG * (TCM / 8) * 128, planeB_bytes = KG * (TCN / 8) * 128;
-  auto issue = [&](uint32_t acc, int si, int ti, bool first) {
-#pragma unroll
-    for (int ks = 0; ks < TCK / 16; ++ks) {
-      // K offset ks*16 = two core-matrix groups
-      const uint64_t a = smem_desc(aBase + si * planeA_bytes + ks * 2 * lboA, lboA, sbo);
-      const uint64_t b = smem_desc(bBase + ti * planeB_bytes + ks * 2 * lboB, lboB, sbo);
-      mma_bf16_tc(acc, a, b, idesc, (first && ks == 0) ? 0u : 1u);
-    }
-  };
-  auto issue_level = [&](uint32_t acc, int L, bool first) {
-    for (int si = max(1, L - S); si <= min(S, L - 1); ++si) {
-      issue(acc, si - 1, L - si - 1, first);
-      first = false;
-    }
-  };
-  auto commit_and_wait = [&]() -> bool {
-    if (tid == 0)
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              smem_u32(&sh.mbar)));
-    uint32_t done = 0;
-    for (int spin = 0; spin < (1 << 22) && !done; ++spin) {
-      asm volatile(
-          "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-          "selp.b32 %0, 1, 0, P;\n\t}\n"
-          : "=r"(done)
-          : "r"(smem_u32(&sh.mbar)), "r"(phase));
-    }
-    phase ^= 1u;
-    const bool bad = __syncthreads_or(!done);
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    return bad;
-  };
-  const float sa = p2f(sh.eA[my_row] - sh.rA[my_row] - 14);
-  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-  auto flush1 = [&](uint32_t acc) {
-#pragma unroll
-    for (int cb = 0; cb < 72; cb += 8) {
-      float v[8];
-      tmem_ld8(acc + lane_off + col0 + cb, v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        two_sum_acc(hi[cb + i], lo[cb + i], v[i] * (sa * sh.sB[col0 + cb + i]));
-    }
-  };
-  if (sh.rescale) {
-    const float fa = p2f(max(sh.dA[my_row], -127));
-#pragma unroll
-    for (int j = 0; j < 72; ++j) {
-      const float f = fa * p2f(max(sh.dB[min(col0 + j, TCN - 1)], -127));
-      hi[j] *= f;
-      lo[j] *= f;
-    }
-  }
-  if (tid == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    issue_level(acc2, 2, true);
-    issue_level(acc3, 3, true);
-    if (S >= 3) issue_level(accl, 4, true);
-  }
-  if (commit_and_wait()) {
-    return true;
-  }
-  if (S >= 3) flush1(accl);
-  // further phases into the same columns: for S = 7 level 5 gets its own exact
-  // phase so that the inexact tail (levels >= 6, below 2^-32 of level 2)
-  // rounds below 2^-53; otherwise levels 5 .. S+1 (below 2^-24) share one.
-  for (int L0 = 5; L0 <= S + 1;) {
-    const int L1 = (S >= 7 && L0 == 5) ? 5 : S + 1;
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      bool first = true;
-      for (int L = L0; L <= L1; ++L) {
-        issue_level(accl, L, first);
-        first = false;
-      }
-    }
-    if (commit_and_wait()) return true;
-    flush1(accl);
-    L0 = L1 + 1;
-  }
-  flush1(acc2);
-  flush1(acc3);
-  // renormalise
-#pragma unroll
-  for (int j = 0; j < 72; ++j) {
-    const float s2 = hi[j] + lo[j];
-    lo[j] = lo[j] - (s2 - hi[j]);
-    hi[j] = s2;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-    return false;
 }
 
 template <int S>
 __global__ void __launch_bounds__(kThr, 1)
-    ozaki_gram_tc_kernel(int64_t n, SegList U, int p, SegList V, int q, int64_t rows_per_slab,
-                         float4* __restrict__ partial) {
+    ozaki_gram_tc_kernel(int64_t n, SegList U, int p, SegList V, int q, int NT,
+                         int64_t blocks_per_slab, const int* __restrict__ EU,
+                         const int* __restrict__ EV, int4* __restrict__ partial) {
+  constexpr int NA = nacc<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  uint16_t* planeA = reinterpret_cast<uint16_t*>(smem_raw);
-  uint16_t* planeB = planeA + (size_t)S * KG * TCM * 8 * 8 / 8;  // S*KG*(TCM/8) core mats * 64 elems
-  TcShared& sh = *reinterpret_cast<TcShared*>(smem_raw + planes_bytes<S>());
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  const uint32_t pa = (uint32_t)planeA_bytes<S>(), pb = (uint32_t)planeB_bytes(NT);
+  // stage st: A planes at aS0 + st * S * pa, B planes at bS0 + st * S * pb
+  const uint32_t aS0 = smem_u32(base), bS0 = smem_u32(base) + 2 * S * pa;
+  const uint32_t raw0 = smem_u32(base) + 2 * S * (pa + pb);
+  constexpr uint32_t rawB = TCK * kGcols * 8;  // bytes per raw stage
+  GramShared& sh = *reinterpret_cast<GramShared*>(base + 2 * S * (pa + pb) + kRaw * rawB);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tp = blockIdx.x * TCM, tq = blockIdx.y * TCN;
-  const int nq = min(TCN, q - tq);             // valid V columns of this tile
-  const int Nmma = (nq + 15) / 16 * 16;        // MMA N (multiple of 16)
-  const int64_t r0 = (int64_t)blockIdx.z * rows_per_slab;
-  const int64_t r1 = min(n, r0 + rows_per_slab);
+  const int tp = blockIdx.x * TCM, tq = blockIdx.y * NT;
+  const int np_ = min(TCM, p - tp), nq_ = min(NT, q - tq);
+  const int64_t nblk = ceil_div(n, kBlock);
+  const int64_t b0 = (int64_t)blockIdx.z * blocks_per_slab;
+  const int64_t b1 = min(nblk, b0 + blocks_per_slab);
+  const int64_t r_begin = b0 * kBlock, r_end = min(n, b1 * kBlock);
+  const int64_t nchunks = ceil_div(r_end - r_begin, TCK);
+  const int ncs = TCM + NT;  // column slots: A columns, then B columns
+  const double* any = U.ptr[0];
 
-  if (tid == 0) {
-    sh.segU = U;
-    sh.segV = V;
+  for (int c = tid; c < kGcols; c += kThr) {
+    const double* ptr = nullptr;
+    long long ld = 0;
+    if (c < TCM && c < np_) seg_col_ptr(U, tp + c, &ptr, &ld);
+    if (c >= TCM && c - TCM < nq_) seg_col_ptr(V, tq + c - TCM, &ptr, &ld);
+    sh.cptr[c] = ptr;
+    sh.cld[c] = ld;
+    sh.R[c] = kEZero;
   }
-  for (int i = tid; i < TCM; i += kThr) sh.rA[i] = kNone;
-  for (int i = tid; i < TCN; i += kThr) sh.rB[i] = kNone;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(&sh.tmem_base)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
+  if (warp == 0) tmem_alloc(smem_u32(&sh.tmem_base));
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sh.mbar)));
+    mbar_init(smem_u32(&sh.mdone[0]), 1);
+    mbar_init(smem_u32(&sh.mdone[1]), 1);
+    sh.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = sh.tmem_base;
-  const uint32_t acc2 = tmem, acc3 = tmem + TCN, accl = tmem + 2 * TCN;
 
-  // flush ownership: warp w reads TMEM lanes 32*(w%4) .. +31 (one output row
-  // per thread) and columns 72*(w/4) .. +71 of the tile
-  const int my_row = 32 * (warp & 3) + lane;
-  const int col0 = 72 * (warp >> 2);
-  float hi[72], lo[72];
+  // prologue: first two chunks in flight
+  for (int g = 0; g < 2; ++g) {
+    if (g < nchunks)
+      gram_stage_raw(sh, ncs, r_begin + (int64_t)g * TCK, r_end, raw0 + g * rawB, tid, any);
+    cp_async_commit();
+  }
+  cp_async_wait1();
+  __syncthreads();
+
+  // flush ownership: TMEM lane = A column my_i, B columns j0 .. j0 + NT/2 - 1
+  const int my_i = 32 * (warp & 3) + lane;
+  const int half = NT / 2;
+  const int j0 = half * (warp >> 2);
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  long long acc[NTMAX / 2];
 #pragma unroll
-  for (int j = 0; j < 72; ++j) hi[j] = lo[j] = 0.f;
-
-  uint32_t phase = 0;
+  for (int j = 0; j < NTMAX / 2; ++j) acc[j] = 0;
   bool failed = false;
-  const uint32_t idesc = instr_desc(TCM, Nmma);
-  const uint32_t aBase = smem_u32(planeA), bBase = smem_u32(planeB);
+  uint32_t started = 0;
+  int64_t gc = 0;  // chunk counter of the slab
+  // cut items of this thread: (column slot, 8-row group), at most two
+  int it_c[2], it_kg[2];
+  uint32_t it_dst[2], it_ps[2];
+  int nit = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int it = tid + h * kThr;
+    it_c[h] = it % ncs;
+    it_kg[h] = it / ncs;
+    if (it < ncs * KG) nit = h + 1;
+    const int c = it_c[h], kg = it_kg[h];
+    it_dst[h] = c < TCM ? (uint32_t)((kg * (TCM / 8) + (c >> 3)) * 128 + (c & 7) * 16)
+                        : (uint32_t)((kg * (NT / 8) + ((c - TCM) >> 3)) * 128 + ((c - TCM) & 7) * 16);
+    it_ps[h] = c < TCM ? pa : pb;
+  }
 
-  for (int64_t r = r0; r < r1; r += TCK) {
-    // ---- 1. chunk exponents: max effective exponent per column over 32 rows
-    for (int it = tid; it < KG * TCM; it += kThr) {
-      const int c = it % TCM, kg = it / TCM;
-      int e = kZero;
-      if (tp + c < p) {
-        int64_t ld;
-        const double* col = seg_col(sh.segU, tp + c, &ld);
+  for (int64_t b = b0; b < b1 && !failed; ++b) {
+    // ---- block start: exponents of this block, reference update
+    for (int c = tid; c < ncs; c += kThr) {
+      const int E = !sh.cptr[c] ? kEZero
+                    : c < TCM    ? EU[b * p + tp + c]
+                                 : EV[b * q + tq + c - TCM];
+      const int Rn = max(sh.R[c], E);
+      sh.dR[c] = Rn - sh.R[c];
+      sh.R[c] = Rn;
+      sh.eCur[c] = E;
+    }
+    __syncthreads();
+    started = 0;
+    const int64_t rb = b * kBlock;
+    for (int ch = 0; ch < kChunksPerBlock; ++ch) {
+      const int64_t r = rb + (int64_t)ch * TCK;
+      if (r >= r_end) break;
+      const uint32_t st = (uint32_t)(gc & 1);
+      const uint32_t raw = raw0 + (uint32_t)(gc % kRaw) * rawB;
+      if (gc >= 2 && !mbar_wait(smem_u32(&sh.mdone[st]), (uint32_t)((gc >> 1) - 1) & 1))
+        sh.fail = 1;
+      // cut the staged chunk: items (column slot, 8-row group)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int64_t row = r + kg * 8 + i;
-          if (row < r1) e = max(e, eff_exp0(col[row * ld]));
+      for (int h = 0; h < 2; ++h) {
+        if (h < nit) {
+          const int c = it_c[h], kg = it_kg[h];
+          double x[8];
+          int E[8];
+          const int Ec = sh.eCur[c];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            ld_shared_f64(raw + (uint32_t)((kg * 8 + i) * kGcols + c) * 8, x[i]);
+            E[i] = Ec;
+          }
+          const uint32_t base_st = c < TCM ? aS0 + st * S * pa : bS0 + st * S * pb;
+          split8<S>(x, E, base_st + it_dst[h], it_ps[h]);
         }
       }
-      sh.emA[kg][c] = e;
-    }
-    for (int it = tid; it < KG * TCN; it += kThr) {
-      const int c = it % TCN, kg = it / TCN;
-      int e = kZero;
-      if (c < nq) {
-        int64_t ld;
-        const double* col = seg_col(sh.segV, tq + c, &ld);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int64_t row = r + kg * 8 + i;
-          if (row < r1) e = max(e, eff_exp0(col[row * ld]));
-        }
+      // chunk gc + 2 into the stage just read by chunk gc - 1
+      if (gc + 2 < nchunks)
+        gram_stage_raw(sh, ncs, r_begin + (gc + 2) * TCK, r_end,
+                       raw0 + (uint32_t)((gc + 2) % kRaw) * rawB, tid, any);
+      cp_async_commit();
+      cp_async_wait1();  // chunk gc + 1 has landed (this thread's copies)
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      if (__syncthreads_or(sh.fail)) {
+        failed = true;
+        break;
       }
-      sh.emB[kg][c] = e;
-    }
-    __syncthreads();
-    if (tid == 0) sh.rescale = 0;
-    __syncthreads();
-    for (int c = tid; c < TCM + TCN; c += kThr) {
-      if (c < TCM) {
-        int e = kZero;
-        for (int kg = 0; kg < KG; ++kg) e = max(e, sh.emA[kg][c]);
-        const int E = e - 1022;
-        const int rn = max(sh.rA[c], E - kWindow);
-        sh.dA[c] = (sh.rA[c] == kNone) ? 0 : sh.rA[c] - rn;
-        if (sh.dA[c] != 0) sh.rescale = 1;
-        sh.rA[c] = rn;
-        sh.eA[c] = E;
-      } else {
-        const int j = c - TCM;
-        int e = kZero;
-        for (int kg = 0; kg < KG; ++kg) e = max(e, sh.emB[kg][j]);
-        const int E = e - 1022;
-        const int rn = max(sh.rB[j], E - kWindow);
-        sh.dB[j] = (sh.rB[j] == kNone) ? 0 : sh.rB[j] - rn;
-        if (sh.dB[j] != 0) sh.rescale = 1;
-        sh.rB[j] = rn;
-        sh.eB[j] = E;
-        sh.sB[j] = p2f(E - rn);
+      if (tid == kIssuer) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        issue_chunk<S>(tmem, NT, aS0 + st * S * pa, bS0 + st * S * pb, started);
+        mma_commit(smem_u32(&sh.mdone[st]));
       }
+      ++gc;
     }
-    __syncthreads();
-    // ---- 2. split into the core-matrix planes (16-byte stores)
-    for (int it = tid; it < KG * TCM; it += kThr) {
-      const int c = it % TCM, kg = it / TCM;
-      const int E = sh.eA[c];
-      int64_t ld = 0;
-      const double* col = (tp + c < p) ? seg_col(sh.segU, tp + c, &ld) : nullptr;
-      stage_core<S>(col, ld, r + kg * 8, r1, E,
-                    planeA + ((size_t)(kg * (TCM / 8) + (c >> 3)) * 64 + (c & 7) * 8),
-                    (size_t)KG * (TCM / 8) * 64);
-    }
-    for (int it = tid; it < KG * TCN; it += kThr) {
-      const int c = it % TCN, kg = it / TCN;
-      const int E = sh.eB[c];
-      int64_t ld = 0;
-      const double* col = (c < nq) ? seg_col(sh.segV, tq + c, &ld) : nullptr;
-      stage_core<S>(col, ld, r + kg * 8, r1, E,
-                    planeB + ((size_t)(kg * (TCN / 8) + (c >> 3)) * 64 + (c & 7) * 8),
-                    (size_t)KG * (TCN / 8) * 64);
-    }
-    // make the generic-proxy stores visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;\n");
-    __syncthreads();
-    if (tc_mma_and_flush<S>(sh, tid, warp, lane, my_row, col0, aBase, bBase, idesc, acc2, acc3,
-                            accl, phase, hi, lo)) {
+    if (failed) break;
+    // ---- block end: wait for the last chunk's MMAs, fold TMEM into int64
+    if (!mbar_wait(smem_u32(&sh.mdone[(gc - 1) & 1]), (uint32_t)((gc - 1) >> 1) & 1)) sh.fail = 1;
+    if (__syncthreads_or(sh.fail)) {
       failed = true;
       break;
     }
-  }
-  // ---- partial result (hi, lo, exponent) of this slab
-  float4* out = partial + (int64_t)blockIdx.z * p * q;
-  const int gi = tp + my_row;
-  if (gi < p) {
-#pragma unroll
-    for (int j = 0; j < 72; ++j) {
-      const int c = col0 + j;
-      if (c < nq) {
-        float4 v;
-        v.x = failed ? __int_as_float(0x7FC00000) : hi[j];
-        v.y = failed ? 0.f : lo[j];
-        v.z = __int_as_float(sh.rA[my_row] + sh.rB[c]);
-        v.w = 0.f;
-        out[(int64_t)gi * q + (tq + c)] = v;
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-  if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(kTmemCols));
-  }
-}
-
-// ---------------------------------------------------------------- update
-// Y = beta Y0 + alpha S C on tcgen05.  A (M = 128 rows of S) x K (32 columns
-// of S per chunk, row exponents per chunk, columns balanced by 2^-colexp[k]);
-// B = alpha C with rows balanced by 2^colexp[k], pre-split once per call into
-// the exact shared-memory plane layout [chunk][ntile][S][KG][TCN/8][8][8] by
-// split_c_tc_kernel, with per-(chunk, column) exponents.
-
-template <int S>
-__global__ void split_c_tc_kernel(const double* __restrict__ C, int64_t ldc, int s, int m,
-                                  int ntiles, double alpha, const int* __restrict__ colexp,
-                                  uint16_t* __restrict__ Cs, int* __restrict__ Ce) {
-  // one warp per (chunk, padded column); lane = k within the chunk
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nchunks = (s + TCK - 1) / TCK;
-  const int ncols = ntiles * TCN;
-  if (w >= nchunks * ncols) return;
-  const int ch = w / ncols, jj = w % ncols;
-  const int tile = jj / TCN, j = jj % TCN;
-  const int k = ch * TCK + lane;
-  double x = 0.0;
-  if (jj < m && k < s) x = ldexp(alpha * C[k + (int64_t)jj * ldc], colexp ? colexp[k] : 0);
-  int e = eff_exp0(x);
+    {
+      const int Ei = sh.eCur[my_i], Ri = sh.R[my_i], di = sh.dR[my_i];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-  const int E = e - 1022;
-  uint16_t dg[S];
-  split_weighted<S>(x, E, dg);
-  const size_t base = (size_t)(ch * ntiles + tile) * S * KG * (TCN / 8) * 64;
-  const int kg = lane >> 3, ng = j >> 3;
+      for (int g = 0; g < NTMAX / 16; ++g) {
+        if (8 * g < half) {
+          float v[NA][8];
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl)
-    Cs[base + (((size_t)sl * KG + kg) * (TCN / 8) + ng) * 64 + (j & 7) * 8 + (lane & 7)] = dg[sl];
-  if (lane == 0) Ce[(ch * ntiles + tile) * TCN + j] = E;
-}
-
-template <int S>
-__global__ void __launch_bounds__(kThr, 1)
-    ozaki_update_tc_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
-                           const uint16_t* __restrict__ Cs, const int* __restrict__ Ce, int m,
-                           int ntiles, double beta, SegList Y0, OutList Y) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  uint16_t* planeA = reinterpret_cast<uint16_t*>(smem_raw);
-  uint16_t* planeB = planeA + (size_t)S * KG * TCM * 8;
-  TcShared& sh = *reinterpret_cast<TcShared*>(smem_raw + planes_bytes<S>());
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = (int)(blockIdx.x % ntiles);
-  const int64_t row0 = (int64_t)(blockIdx.x / ntiles) * TCM;
-  const int tn = tile * TCN;
-  const int nq = min(TCN, m - tn);
-  const int Nmma = (nq + 15) / 16 * 16;
-  const int nchunks = (s + TCK - 1) / TCK;
-
-  if (tid == 0) sh.segU = Sg;
-  for (int i = tid; i < TCM; i += kThr) sh.rA[i] = kNone;
-  for (int i = tid; i < TCN; i += kThr) sh.rB[i] = kNone;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(&sh.tmem_base)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sh.mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;\n");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
-  const uint32_t tmem = sh.tmem_base;
-  const uint32_t acc2 = tmem, acc3 = tmem + TCN, accl = tmem + 2 * TCN;
-  const int my_row = 32 * (warp & 3) + lane;
-  const int col0 = 72 * (warp >> 2);
-  float hi[72], lo[72];
+          for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + j0 + 8 * g, v[a]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 72; ++j) hi[j] = lo[j] = 0.f;
-  uint32_t phase = 0;
-  bool failed = false;
-  const uint32_t idesc = instr_desc(TCM, Nmma);
-  const uint32_t aBase = smem_u32(planeA), bBase = smem_u32(planeB);
-
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int k0 = ch * TCK;
-    // ---- row exponents of the balanced S chunk (items: row x 8 consecutive k)
-    for (int it = tid; it < KG * TCM; it += kThr) {
-      const int rl = it % TCM, kg = it / TCM;
-      const int64_t row = row0 + rl;
-      int e = kZero;
-      if (row < n) {
+          for (int i = 0; i < 8; ++i) {
+            const int cj = TCM + j0 + 8 * g + i;
+            float w[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int k = k0 + kg * 8 + i;
-          if (k < s) {
-            int64_t ld;
-            const double* col = seg_col(sh.segU, k, &ld);
-            const double x = col[row * ld];
-            const int ee = eff_exp0(x);
-            if (ee != kZero) e = max(e, ee - (colexp ? colexp[k] : 0));
+            for (int a = 0; a < NA; ++a) w[a] = v[a][i];
+            const long long T = acc_to_i64<S>(w);
+            const int shift = Ri + sh.R[cj] - Ei - sh.eCur[cj];
+            acc[8 * g + i] = shr_sat(acc[8 * g + i], di + sh.dR[cj]) + shr_sat(T, shift);
           }
         }
       }
-      sh.emA[kg][rl] = e;
     }
-    // ---- B planes and exponents of this chunk / column tile (pre-split)
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(
-          Cs + (size_t)(ch * ntiles + tile) * S * KG * (TCN / 8) * 64);
-      uint4* dst = reinterpret_cast<uint4*>(planeB);
-      const int nvec = S * KG * (TCN / 8) * 64 / 8;
-      for (int v = tid; v < nvec; v += kThr) dst[v] = src[v];
-      for (int j = tid; j < TCN; j += kThr) sh.eB[j] = Ce[(ch * ntiles + tile) * TCN + j];
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
-    if (tid == 0) sh.rescale = 0;
-    __syncthreads();
-    for (int c = tid; c < TCM + TCN; c += kThr) {
-      if (c < TCM) {
-        int e = kZero;
-        for (int kg = 0; kg < KG; ++kg) e = max(e, sh.emA[kg][c]);
-        const int E = e - 1022;
-        const int rn = max(sh.rA[c], E - kWindow);
-        sh.dA[c] = (sh.rA[c] == kNone) ? 0 : sh.rA[c] - rn;
-        if (sh.dA[c] != 0) sh.rescale = 1;
-        sh.rA[c] = rn;
-        sh.eA[c] = E;
-      } else {
-        const int j = c - TCM;
-        const int E = sh.eB[j];
-        const int rn = max(sh.rB[j], E - kWindow);
-        sh.dB[j] = (sh.rB[j] == kNone) ? 0 : sh.rB[j] - rn;
-        if (sh.dB[j] != 0) sh.rescale = 1;
-        sh.rB[j] = rn;
-        sh.sB[j] = p2f(E - rn);
-      }
-    }
-    __syncthreads();
-    // ---- split the S chunk into the A planes
-    for (int it = tid; it < KG * TCM; it += kThr) {
-      const int rl = it % TCM, kg = it / TCM;
-      const int64_t row = row0 + rl;
-      const int E = sh.eA[rl];
-      uint32_t w[S][4];
+  }
+  cp_async_wait0();  // no copy may outlive the CTA
+  // ---- slab partial: (value, exponent) = acc * 2^(R_i + R_j - 14 - kFrac)
+  if (my_i < np_) {
+    int4* out = partial + ((int64_t)blockIdx.z * p + tp + my_i) * q + tq;
+#pragma unroll
+    for (int g = 0; g < NTMAX / 16; ++g)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int k = k0 + kg * 8 + i;
-        double x = 0.0;
-        int cs = 0;
-        if (row < n && k < s) {
-          int64_t ld;
-          const double* col = seg_col(sh.segU, k, &ld);
-          x = col[row * ld];
-          cs = colexp ? colexp[k] : 0;
-        }
-        uint16_t dg[S];
-        split_weighted<S>(x, E + cs, dg);
-#pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-          if (i & 1)
-            w[sl][i >> 1] |= (uint32_t)dg[sl] << 16;
-          else
-            w[sl][i >> 1] = dg[sl];
+        const int j = j0 + 8 * g + i;
+        if (8 * g < half && j < nq_) {
+          const long long v = failed ? 0 : acc[8 * g + i];
+          int4 w;
+          w.x = (int)(unsigned)(unsigned long long)v;
+          w.y = (int)(v >> 32);
+          w.z = sh.R[my_i] + sh.R[TCM + j] - 14 - kFrac;
+          w.w = failed ? 1 : 0;
+          out[j] = w;
         }
       }
-      uint16_t* dst = planeA + ((size_t)(kg * (TCM / 8) + (rl >> 3)) * 64 + (rl & 7) * 8);
-#pragma unroll
-      for (int sl = 0; sl < S; ++sl)
-        *reinterpret_cast<uint4*>(dst + (size_t)sl * KG * (TCM / 8) * 64) =
-            make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n");
-    __syncthreads();
-    if (tc_mma_and_flush<S>(sh, tid, warp, lane, my_row, col0, aBase, bBase, idesc, acc2, acc3,
-                            accl, phase, hi, lo)) {
-      failed = true;
-      break;
-    }
-  }
-  // ---- output rows: Y = (hi + lo) 2^(rA + rB) + beta Y0
-  const int64_t row = row0 + my_row;
-  if (row < n) {
-#pragma unroll
-    for (int j = 0; j < 72; ++j) {
-      const int c = tn + col0 + j;
-      if (col0 + j < nq) {
-        const double y0 = beta != 0.0 ? seg_load(Y0, c, row) : 0.0;
-        *out_addr(Y, c, row) =
-            failed ? __longlong_as_double(0x7FF8000000000000LL)
-                   : assemble_df(hi[j], lo[j], sh.rA[my_row] + sh.rB[col0 + j], y0);
-      }
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(kTmemCols));
+    tmem_dealloc(tmem);
   }
 }
 
-template <int S>
-size_t tc_smem_bytes() {
-  return planes_bytes<S>() + sizeof(TcShared) + 64;
+// G(i, j) = sum over slabs of the int64 partials, aligned and summed in 128-bit
+// integers in slab order (deterministic), rounded once to FP64.
+__global__ void gram_tc_reduce_kernel(const int4* __restrict__ partial, int slabs, int p, int q,
+                                      double* __restrict__ G, int64_t ldg) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)p * q) return;
+  const int i = (int)(idx / q), j = (int)(idx % q);
+  int emax = -2000000000;
+  bool bad = false;
+  for (int s = 0; s < slabs; ++s) {
+    const int4 w = partial[((int64_t)s * p + i) * q + j];
+    bad |= w.w != 0;
+    if (w.x != 0 || w.y != 0) emax = max(emax, w.z);
+  }
+  double out = 0.0;
+  if (bad) {
+    out = __longlong_as_double(0x7FF8000000000000LL);
+  } else if (emax > -2000000000) {
+    __int128 sum = 0;
+    for (int s = 0; s < slabs; ++s) {
+      const int4 w = partial[((int64_t)s * p + i) * q + j];
+      const long long v = ((long long)w.y << 32) | (long long)(unsigned)w.x;
+      if (v == 0) continue;
+      const int k = emax - w.z;  // >= 0
+      if (k < 100) sum += (((__int128)v) << 56) >> k;
+    }
+    if (sum != 0) {
+      const bool neg = sum < 0;
+      const unsigned __int128 a = neg ? (unsigned __int128)(-sum) : (unsigned __int128)sum;
+      const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+      const int top = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+      const int sh = top > 62 ? top - 62 : 0;
+      unsigned long long m = (unsigned long long)(a >> sh);
+      if (sh > 0 && (a & ((((unsigned __int128)1) << sh) - 1)) != 0) m |= 1;  // sticky
+      out = int_to_double(neg ? -(long long)m : (long long)m, emax - 56 + sh);
+    }
+  }
+  G[i + (int64_t)j * ldg] = out;
 }
 
-void tc_plan(int64_t n, int p, int q, int* slabs, int64_t* rows_per_slab) {
-  const int64_t tiles = ceil_div(p, TCM) * ceil_div(q, TCN);
-  int64_t s = std::max<int64_t>(1, ceil_div(152, tiles));
-  s = std::min<int64_t>(s, std::max<int64_t>(1, ceil_div(n, 8 * TCK)));
-  int64_t r = round_up(ceil_div(std::max<int64_t>(n, 1), s), TCK);
-  s = std::max<int64_t>(1, ceil_div(std::max<int64_t>(n, 1), r));
-  *slabs = (int)s;
-  *rows_per_slab = r;
+void gram_tiles(int q, int* ntq, int* NT) {
+  *ntq = (int)ceil_div(q, NTMAX);
+  *NT = (int)round_up(ceil_div(q, *ntq), 16);
+}
+
+void gram_plan(int64_t n, int p, int q, int* slabs, int64_t* per_slab) {
+  int ntq, NT;
+  gram_tiles(q, &ntq, &NT);
+  const int64_t tiles = ceil_div(p, TCM) * ntq;
+  const int64_t nblk = std::max<int64_t>(1, ceil_div(n, kBlock));
+  // one wave of CTAs; at most 64 blocks per slab keeps the int64 sums < 2^61
+  int64_t s = std::max<int64_t>(ceil_div(152, tiles), ceil_div(nblk, 64));
+  s = std::min(s, nblk);
+  const int64_t per = ceil_div(nblk, s);
+  *slabs = (int)ceil_div(nblk, per);
+  *per_slab = per;
 }
 
 template <int S>
-int tc_launch(cudaStream_t st, int64_t n, const SegList& U, int p, const SegList& V, int q,
-              int slabs, int64_t rps, float4* partial) {
-  const size_t sh = tc_smem_bytes<S>();
+int gram_tc_launch(cudaStream_t st, int64_t n, const SegList& U, int p, const SegList& V, int q,
+                   int slabs, int64_t per, const int* EU, const int* EV, int4* partial) {
+  int ntq, NT;
+  gram_tiles(q, &ntq, &NT);
+  const size_t sh = gram_smem_bytes<S>(NTMAX);
   static bool configured = false;
   if (!configured) {
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_gram_tc_kernel<S>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     configured = true;
   }
-  dim3 grid((unsigned)ceil_div(p, TCM), (unsigned)ceil_div(q, TCN), (unsigned)slabs);
-  ozaki_gram_tc_kernel<S><<<grid, kThr, sh, st>>>(n, U, p, V, q, rps, partial);
+  dim3 grid((unsigned)ceil_div(p, TCM), (unsigned)ntq, (unsigned)slabs);
+  ozaki_gram_tc_kernel<S><<<grid, kThr, gram_smem_bytes<S>(NT), st>>>(n, U, p, V, q, NT, per, EU,
+                                                                      EV, partial);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
+// ----------------------------------------------------------------- update
+// Y = beta Y0 + alpha S C.  A = S (M = 128 rows, K = s columns; one exponent
+// per row over all columns of the balanced S(i, k) 2^-colexp[k]), B = alpha C
+// with rows scaled by 2^colexp[k] (one exponent per column over all k), cut
+// once per call by split_c_tc_kernel into the shared-memory plane layout
+// [chunk][tile][S][KG][NT/8][8][8].  Persistent CTAs walk the (row block,
+// column tile) pairs; the row exponents of a CTA's next tile are computed
+// during its current tile.
+
+template <int S>
+__global__ void split_c_tc_kernel(const double* __restrict__ C, int64_t ldc, int s, int m,
+                                  int ntiles, int NT, double alpha, const int* __restrict__ colexp,
+                                  uint16_t* __restrict__ Cs, int* __restrict__ Ce) {
+  // one warp per padded column; lanes over k
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int ncols = ntiles * NT;
+  if (w >= ncols) return;
+  const int tile = w / NT, j = w % NT;
+  const int nch = (int)ceil_div(s, TCK);
+  auto val = [&](int k) -> double {
+    if (w >= m || k >= s) return 0.0;
+    return ldexp(alpha * C[k + (int64_t)w * ldc], colexp ? colexp[k] : 0);
+  };
+  int e = 0;  // biased exponent maximum; 0 = all zero
+  for (int k = lane; k < s; k += 32) {
+    const double x = val(k);
+    if (x != 0.0) e = max(e, max((int)((__double_as_longlong(x) >> 52) & 0x7FF), 1));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  const int E = e ? e - 1022 : kEZero;
+  if (lane == 0) Ce[w] = E;
+  const size_t blk = (size_t)S * KG * (NT / 8) * 64;  // bf16 per (chunk, tile)
+  for (int k = lane; k < nch * TCK; k += 32) {
+    float d[S];
+    digits<S>(val(k), E, d);
+    const int ch = k / TCK, kk = k % TCK;
+    uint16_t* dst = Cs + (size_t)(ch * ntiles + tile) * blk;
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl)
+      dst[(((size_t)sl * KG + (kk >> 3)) * (NT / 8) + (j >> 3)) * 64 + (j & 7) * 8 + (kk & 7)] =
+          (uint16_t)(__float_as_uint(d[sl]) >> 16);
+  }
+}
+
+constexpr int kRawRow = TCK + 1;  // raw row pitch in doubles (odd: conflict-free 8-byte reads)
+
+struct UpdShared {
+  unsigned long long bfull[2], mdone[2];
+  uint32_t tmem_base;
+  int fail;
+  int eA[TCM];     // row exponent bounds of the balanced S, current tile
+  int eC[NTMAX];   // column exponent bounds of the balanced C, current tile
+  SegList seg;
+};
+
+// ER[i] = exponent bound of row i of the balanced S(i, k) 2^-colexp[k] over all
+// k (kEZero for a zero row).  One warp per row, lanes over k.
+__global__ void row_exp_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
+                               int* __restrict__ ER) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  int e = -1000000;
+  for (int k0 = 0; k0 < s; k0 += 128) {
+    double x[4];
+    int cxk[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = k0 + 32 * i + lane;
+      x[i] = 0.0;
+      cxk[i] = 0;
+      if (k < s) {
+        const double* p;
+        long long ld;
+        seg_col_ptr(Sg, k, &p, &ld);
+        x[i] = __ldg(p + row * ld);
+        cxk[i] = colexp ? __ldg(colexp + k) : 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long b = __double_as_longlong(x[i]);
+      if ((b << 1) != 0) e = max(e, max((int)((b >> 52) & 0x7FF), 1) - cxk[i]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) ER[row] = e > -1000000 ? e - 1022 : kEZero;
+}
+
+
+__device__ __forceinline__ void upd_k(const UpdShared& sh, int k, const double** p,
+                                      long long* ld) {
+  seg_col_ptr(sh.seg, k, p, ld);
+}
+
+// Stage S(rows row0 .. row0 + 127, columns kc .. kc + TCK - 1) into raw
+// ([TCM][kRawRow]); zero outside the matrix.
+__device__ __forceinline__ void upd_stage_raw(const UpdShared& sh, int64_t n, int s, int64_t row0,
+                                              int kc, uint32_t raw, int tid) {
+  // thread: column kk = tid % TCK, rows tid / TCK + 16 j (coalesced along k)
+  const int kk = tid % TCK, r0 = tid / TCK;
+  const int k = kc + kk;
+  const double* p;
+  long long ld;
+  upd_k(sh, k < s ? k : 0, &p, &ld);
+  const double* src = p + (row0 + r0) * ld;
+  const long long step = (long long)(kThr / TCK) * ld;
+#pragma unroll
+  for (int j = 0; j < TCM * TCK / kThr; ++j) {
+    const int rl = r0 + j * (kThr / TCK);
+    const bool ok = k < s && row0 + rl < n;
+    cp_async8(raw + (uint32_t)(rl * kRawRow + kk) * 8, ok ? src : p, ok);
+    src += step;
+  }
+}
+
+constexpr int kThrAll = kThr + 32;  // 8 compute warps + 1 issuer warp
+constexpr int kIssuerW = kThr;      // issuer thread of the update (warp 8, lane 0)
+constexpr int kOutRows = 64;        // rows of the output staging pass
+
+template <int S>
+__host__ __device__ inline size_t upd_regionA(int NT) {
+  const size_t a = 2 * S * planeA_bytes<S>(), o = (size_t)kOutRows * (NT + 1) * 8;
+  return ((a > o ? a : o) + 1023) / 1024 * 1024;
+}
+
+template <int S>
+size_t upd_smem_bytes(int NT, int s) {
+  return upd_regionA<S>(NT) + 2 * S * planeB_bytes(NT) + (size_t)kRaw * TCM * kRawRow * 8 +
+         sizeof(UpdShared) + (size_t)round_up(std::max(s, 1), 4) * 4 + 1024;
+}
+
+// kOneBlock: s <= 256, a single exponent block; the TMEM accumulators go
+// straight to the output (no int64 carry registers).
+template <int S, bool kOneBlock>
+__global__ void __launch_bounds__(kThrAll, 1)
+    ozaki_update_tc_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
+                           const uint16_t* __restrict__ Cs, const int* __restrict__ Ce,
+                           const int* __restrict__ ER, int m, int ntiles, int NT,
+                           int64_t ntile_total, double beta, SegList Y0, OutList Y) {
+  constexpr int NA = nacc<S>();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  const uint32_t pa = (uint32_t)planeA_bytes<S>(), pb = (uint32_t)planeB_bytes(NT);
+  const size_t regA = upd_regionA<S>(NT);
+  // region A: the A planes of both stages, reused as the output staging area
+  const uint32_t aS0 = smem_u32(base), bS0 = smem_u32(base) + (uint32_t)regA;
+  double* ostage = reinterpret_cast<double*>(base);
+  const int OP = NT + 1;  // output staging pitch (odd: conflict-free row-wise writes)
+  const uint32_t raw0 = bS0 + 2 * S * pb;
+  constexpr uint32_t rawB = TCM * kRawRow * 8;
+  unsigned char* after_raw = base + regA + 2 * S * pb + kRaw * rawB;
+  UpdShared& sh = *reinterpret_cast<UpdShared*>(after_raw);
+  int* cx = reinterpret_cast<int*>(after_raw + sizeof(UpdShared));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool compute = tid < kThr;
+  const int nch = (int)ceil_div(s, TCK);
+  const size_t cs_blk = (size_t)S * KG * (NT / 8) * 64;  // bf16 per (chunk, tile)
+  const uint32_t bbytes = (uint32_t)(cs_blk * 2);
+
+  if (warp == 0) tmem_alloc(smem_u32(&sh.tmem_base));
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&sh.bfull[i]), 1);
+      mbar_init(smem_u32(&sh.mdone[i]), 1);
+    }
+    sh.fail = 0;
+    sh.seg = Sg;
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  for (int k = tid; k < s; k += kThrAll) cx[k] = colexp ? colexp[k] : 0;
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = sh.tmem_base;
+
+  const int my_r = 32 * (warp & 3) + lane;  // TMEM lane = tile row (compute threads)
+  const int half = NT / 2;
+  const int j0 = half * ((warp >> 2) & 1);
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  bool failed = false;
+  int64_t gc = 0;  // chunk counter of this CTA over all its tiles
+  const int64_t t0 = blockIdx.x, tstep = gridDim.x;
+  auto tile_row0 = [&](int64_t t) { return (t / ntiles) * TCM; };
+  const int64_t my_chunks = ((ntile_total - t0 + tstep - 1) / tstep) * nch;
+  // chunk g of this CTA: tile t0 + (g / nch) tstep, columns (g % nch) TCK
+  auto stage = [&](int64_t g) {
+    if (g < my_chunks) {
+      const int64_t t = t0 + (g / nch) * tstep;
+      upd_stage_raw(sh, n, s, tile_row0(t), (int)(g % nch) * TCK,
+                    raw0 + (uint32_t)(g % kRaw) * rawB, tid);
+    }
+    cp_async_commit();
+  };
+  auto load_b = [&](int64_t g) {  // issuer: B digits of chunk g into stage g & 1
+    const int64_t t = t0 + (g / nch) * tstep;
+    const uint32_t st = (uint32_t)(g & 1);
+    const size_t src = ((size_t)(g % nch) * ntiles + (size_t)(t % ntiles)) * cs_blk;
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
+                 : "=l"(state)
+                 : "r"(smem_u32(&sh.bfull[st])), "r"(bbytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];\n" ::"r"(bS0 + st * S * pb),
+        "l"(Cs + src), "r"(bbytes), "r"(smem_u32(&sh.bfull[st]))
+        : "memory");
+  };
+  int64_t b_issued = -1;  // last chunk whose B copy the issuer started
+  if (compute) {
+    stage(0);
+    stage(1);
+    cp_async_wait1();
+  } else if (tid == kIssuerW && my_chunks > 0) {
+    load_b(0);
+    b_issued = 0;
+  }
+  __syncthreads();
+
+  for (int64_t t = t0; t < ntile_total && !failed; t += tstep) {
+    const int tile = (int)(t % ntiles);
+    const int64_t row0 = tile_row0(t);
+    const int tn = tile * NT;
+    const int nq_ = min(NT, m - tn);
+    for (int r = tid; r < TCM; r += kThrAll) sh.eA[r] = row0 + r < n ? ER[row0 + r] : kEZero;
+    for (int j = tid; j < NTMAX; j += kThrAll) sh.eC[j] = j < NT ? Ce[tn + j] : kEZero;
+    __syncthreads();
+    long long acc[kOneBlock ? 1 : NTMAX / 2];
+#pragma unroll
+    for (int j = 0; j < (kOneBlock ? 1 : NTMAX / 2); ++j) acc[j] = 0;
+    uint32_t started = 0;
+    for (int kc = 0; kc < s && !failed; kc += kBlock) {  // blocks of 256 columns
+      started = 0;
+      const int kend = min(s, kc + kBlock);
+      const bool last_block = kend >= s;
+      for (int k1 = kc; k1 < kend; k1 += TCK) {
+        const uint32_t st = (uint32_t)(gc & 1);
+        if (compute) {
+          const uint32_t raw = raw0 + (uint32_t)(gc % kRaw) * rawB;
+          if (gc >= 2 && !mbar_wait(smem_u32(&sh.mdone[st]), (uint32_t)((gc >> 1) - 1) & 1))
+            sh.fail = 1;
+          // cut the staged chunk: item (row, 8-column group) = (tid % 128, tid / 128)
+          {
+            const int rl = tid % TCM, kg = tid / TCM;
+            double x[8];
+            int E[8];
+            const int Er = sh.eA[rl];
+            const uint32_t src = raw + (uint32_t)(rl * kRawRow + kg * 8) * 8;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              ld_shared_f64(src + 8 * i, x[i]);
+              const int k = k1 + kg * 8 + i;
+              E[i] = Er + (k < s ? cx[k] : 0);
+            }
+            split8<S>(x, E,
+                      aS0 + st * S * pa +
+                          (uint32_t)((kg * (TCM / 8) + (rl >> 3)) * 128 + (rl & 7) * 16),
+                      pa);
+          }
+          stage(gc + 2);
+          cp_async_wait1();
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        }
+        if (__syncthreads_or(sh.fail)) {
+          failed = true;
+          break;
+        }
+        if (tid == kIssuerW) {
+          if (!mbar_wait(smem_u32(&sh.bfull[st]), (uint32_t)(gc >> 1) & 1)) {
+            sh.fail = 1;
+          } else {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            issue_chunk<S>(tmem, NT, aS0 + st * S * pa, bS0 + st * S * pb, started);
+            mma_commit(smem_u32(&sh.mdone[st]));
+            // B of the next chunk into the other stage, once chunk gc - 1 is done
+            if (gc + 1 < my_chunks) {
+              if (gc >= 1 &&
+                  !mbar_wait(smem_u32(&sh.mdone[st ^ 1]), (uint32_t)((gc - 1) >> 1) & 1)) {
+                sh.fail = 1;
+              } else {
+                load_b(gc + 1);
+                b_issued = gc + 1;
+              }
+            }
+          }
+        }
+        ++gc;
+      }
+      if (failed) break;
+      if (!mbar_wait(smem_u32(&sh.mdone[(gc - 1) & 1]), (uint32_t)((gc - 1) >> 1) & 1))
+        sh.fail = 1;
+      if (__syncthreads_or(sh.fail)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      if (!last_block) {
+        if (!kOneBlock && compute) {
+#pragma unroll
+          for (int g = 0; g < NTMAX / 16; ++g) {
+            if (8 * g < half) {
+              float v[NA][8];
+#pragma unroll
+              for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + j0 + 8 * g, v[a]);
+              asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                float w[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < NA; ++a) w[a] = v[a][i];
+                if (!kOneBlock) acc[(8 * g + i) % (kOneBlock ? 1 : NTMAX / 2)] += acc_to_i64<S>(w);
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+      }
+    }
+    // ---- output: Y = acc 2^(E_row + E_col - 14 - kFrac) + beta Y0, in two
+    // passes of 64 rows staged through shared memory (coalesced Y0 and Y)
+    for (int h = 0; h < TCM / kOutRows; ++h) {
+      const int64_t rbase = row0 + h * kOutRows;
+      if (beta != 0.0 && compute && !failed) {
+        for (int rr = warp; rr < kOutRows; rr += kThr / 32) {
+          const int64_t row = rbase + rr;
+          if (row < n)
+            for (int j = lane; j < nq_; j += 32) ostage[rr * OP + j] = seg_load(Y0, tn + j, row);
+        }
+      }
+      __syncthreads();
+      if (compute && ((warp & 3) >> 1) == h) {
+        const int rr = my_r - h * kOutRows;
+        const int Er = sh.eA[my_r];
+#pragma unroll
+        for (int g = 0; g < NTMAX / 16; ++g) {
+          if (8 * g < half) {
+            float v[NA][8];
+            if (!failed) {
+#pragma unroll
+              for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + j0 + 8 * g, v[a]);
+              asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int j = j0 + 8 * g + i;
+              if (j < nq_) {
+                double out = __longlong_as_double(0x7FF8000000000000LL);
+                if (!failed) {
+                  float w[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                  for (int a = 0; a < NA; ++a) w[a] = v[a][i];
+                  long long T = acc_to_i64<S>(w);
+                  if (!kOneBlock) T += acc[(8 * g + i) % (kOneBlock ? 1 : NTMAX / 2)];
+                  const double y0 = beta != 0.0 ? ostage[rr * OP + j] : 0.0;
+                  out = assemble_i64(T, Er + sh.eC[j] - 14 - kFrac, y0);
+                }
+                ostage[rr * OP + j] = out;
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      __syncthreads();
+      if (compute) {
+        for (int rr = warp; rr < kOutRows; rr += kThr / 32) {
+          const int64_t row = rbase + rr;
+          if (row < n)
+            for (int j = lane; j < nq_; j += 32) *out_addr(Y, tn + j, row) = ostage[rr * OP + j];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (compute) cp_async_wait0();  // no copy may outlive the CTA
+  if (tid == kIssuerW && b_issued >= 0 && failed)
+    mbar_wait(smem_u32(&sh.bfull[b_issued & 1]), (uint32_t)(b_issued >> 1) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    tmem_dealloc(tmem);
+  }
+}
+
+void update_tiles(int m, int* ntiles, int* NT) {
+  *ntiles = (int)ceil_div(std::max(m, 1), NTMAX);
+  *NT = (int)round_up(ceil_div(std::max(m, 1), *ntiles), 16);
+}
+
+template <int S>
+int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const double* C,
+                     int64_t ldc, int m, double alpha, double beta, const SegList& Y0,
+                     const OutList& Y, const int* colexp, void* work) {
+  int ntiles, NT;
+  update_tiles(m, &ntiles, &NT);
+  const int nch = (int)ceil_div(s, TCK);
+  uint16_t* Cs = (uint16_t*)work;
+  const size_t cs_elems = (size_t)nch * ntiles * S * KG * (NT / 8) * 64;
+  int* Ce = (int*)(Cs + cs_elems);
+  int* cxw = Ce + (size_t)ntiles * NT;
+  int* ER = cxw + s;
+  if (!colexp) {
+    int rc = column_exponents(st, n, Sg, s, cxw);
+    if (rc) return rc;
+    colexp = cxw;
+  }
+  row_exp_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, Sg, s, colexp, ER);
+  LOB_LAUNCHED();
+  {
+    const int64_t warps = (int64_t)ntiles * NT;
+    split_c_tc_kernel<S><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
+        C, ldc, s, m, ntiles, NT, alpha, colexp, Cs, Ce);
+    LOB_LAUNCHED();
+  }
+  const size_t shmax = upd_smem_bytes<S>(NTMAX, kMaxUpdateK);
+  static bool configured = false;
+  if (!configured) {
+    LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
+    LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
+    configured = true;
+  }
+  const int64_t tiles = ceil_div(n, TCM) * ntiles;
+  const int64_t grid = std::min<int64_t>(tiles, 152);
+  if (s <= kBlock)
+    ozaki_update_tc_kernel<S, true><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
+        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y);
+  else
+    ozaki_update_tc_kernel<S, false><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
+        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y);
   LOB_LAUNCHED();
   return LOBPCG_OK;
 }
@@ -690,9 +1081,10 @@ int tc_launch(cudaStream_t st, int64_t n, const SegList& U, int p, const SegList
 
 int64_t gram_tc_workspace(int64_t n, int p, int q) {
   int slabs;
-  int64_t r;
-  tc_plan(n, p, q, &slabs, &r);
-  return (int64_t)slabs * p * q * (int64_t)sizeof(float4);
+  int64_t per;
+  gram_plan(n, p, q, &slabs, &per);
+  const int64_t nblk = std::max<int64_t>(1, ceil_div(n, kBlock));
+  return (int64_t)slabs * p * q * (int64_t)sizeof(int4) + nblk * (p + q) * 4;
 }
 
 int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, double* G,
@@ -702,72 +1094,43 @@ int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, doub
   if (slices == 0) slices = 6;
   if (n <= 0) return gram_ozaki(st, n, U, V, G, ldg, slices, work, work_bytes);
   int slabs;
-  int64_t rps;
-  tc_plan(n, p, q, &slabs, &rps);
-  if (work_bytes < (int64_t)slabs * p * q * (int64_t)sizeof(float4)) return LOBPCG_ERR_ARG;
-  float4* partial = (float4*)work;
+  int64_t per;
+  gram_plan(n, p, q, &slabs, &per);
+  if (work_bytes < gram_tc_workspace(n, p, q)) return LOBPCG_ERR_ARG;
+  if (slices < 3 || slices > 7) return LOBPCG_ERR_ARG;
+  int4* partial = (int4*)work;
+  const int64_t nblk = ceil_div(n, kBlock);
+  int* EU = (int*)(partial + (int64_t)slabs * p * q);
+  int* EV = EU + nblk * p;
+  block_col_exp_kernel<<<dim3((unsigned)ceil_div(p, 32), (unsigned)ceil_div(nblk, 8)), 256, 0,
+                         st>>>(n, U, p, nblk, EU);
+  LOB_LAUNCHED();
+  block_col_exp_kernel<<<dim3((unsigned)ceil_div(q, 32), (unsigned)ceil_div(nblk, 8)), 256, 0,
+                         st>>>(n, V, q, nblk, EV);
+  LOB_LAUNCHED();
   int rc;
   switch (slices) {
-    case 3: rc = tc_launch<3>(st, n, U, p, V, q, slabs, rps, partial); break;
-    case 4: rc = tc_launch<4>(st, n, U, p, V, q, slabs, rps, partial); break;
-    case 5: rc = tc_launch<5>(st, n, U, p, V, q, slabs, rps, partial); break;
-    case 6: rc = tc_launch<6>(st, n, U, p, V, q, slabs, rps, partial); break;
-    case 7: rc = tc_launch<7>(st, n, U, p, V, q, slabs, rps, partial); break;
-    default: return LOBPCG_ERR_ARG;
+    case 3: rc = gram_tc_launch<3>(st, n, U, p, V, q, slabs, per, EU, EV, partial); break;
+    case 4: rc = gram_tc_launch<4>(st, n, U, p, V, q, slabs, per, EU, EV, partial); break;
+    case 5: rc = gram_tc_launch<5>(st, n, U, p, V, q, slabs, per, EU, EV, partial); break;
+    case 6: rc = gram_tc_launch<6>(st, n, U, p, V, q, slabs, per, EU, EV, partial); break;
+    default: rc = gram_tc_launch<7>(st, n, U, p, V, q, slabs, per, EU, EV, partial); break;
   }
   if (rc) return rc;
-  return ozaki_slab_reduce(st, partial, slabs, p, q, G, ldg);
-}
-
-}  // namespace lob
-
-namespace lob {
-
-namespace {
-
-template <int S>
-int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const double* C,
-                     int64_t ldc, int m, double alpha, double beta, const SegList& Y0,
-                     const OutList& Y, const int* colexp, void* work) {
-  const int ntiles = (int)ceil_div(m, TCN);
-  const int nchunks = (int)ceil_div(s, TCK);
-  uint16_t* Cs = (uint16_t*)work;
-  const size_t cs_elems = (size_t)nchunks * ntiles * S * KG * (TCN / 8) * 64;
-  int* Ce = (int*)(Cs + cs_elems);
-  int* cx = Ce + (size_t)nchunks * ntiles * TCN;
-  if (!colexp) {
-    int rc = column_exponents(st, n, Sg, s, cx);
-    if (rc) return rc;
-    colexp = cx;
-  }
-  {
-    const int64_t warps = (int64_t)nchunks * ntiles * TCN;
-    split_c_tc_kernel<S><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
-        C, ldc, s, m, ntiles, alpha, colexp, Cs, Ce);
-    LOB_LAUNCHED();
-  }
-  const size_t sh = tc_smem_bytes<S>();
-  static bool configured = false;
-  if (!configured) {
-    LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    configured = true;
-  }
-  const int64_t blocks = ceil_div(n, TCM) * ntiles;
-  ozaki_update_tc_kernel<S><<<(unsigned)blocks, kThr, sh, st>>>(n, Sg, s, colexp, Cs, Ce, m,
-                                                                ntiles, beta, Y0, Y);
+  const int64_t total = (int64_t)p * q;
+  gram_tc_reduce_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(partial, slabs, p, q, G,
+                                                                         ldg);
   LOB_LAUNCHED();
   return LOBPCG_OK;
 }
 
-}  // namespace
-
-int64_t update_tc_workspace(int64_t, int s, int m, int slices) {
+int64_t update_tc_workspace(int64_t n, int s, int m, int slices) {
   if (slices == 0) slices = 6;
-  const int64_t ntiles = ceil_div(std::max(m, 1), TCN);
-  const int64_t nchunks = ceil_div(std::max(s, 1), TCK);
-  return nchunks * ntiles * slices * KG * (TCN / 8) * 64 * 2 + nchunks * ntiles * TCN * 4 +
-         (int64_t)std::max(s, 1) * 4 + 256;
+  int ntiles, NT;
+  update_tiles(m, &ntiles, &NT);
+  const int64_t nch = ceil_div(std::max(s, 1), TCK);
+  return nch * ntiles * slices * KG * (NT / 8) * 64 * 2 + (int64_t)ntiles * NT * 4 +
+         (int64_t)std::max(s, 1) * 4 + std::max<int64_t>(n, 1) * 4 + 256;
 }
 
 int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc, int m,
@@ -777,6 +1140,7 @@ int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int
   if (n <= 0 || m <= 0) return LOBPCG_OK;
   if (slices == 0) slices = 6;
   if (s == 0) return update_f64(st, n, S, C, ldc, m, alpha, beta, Y0, Y);
+  if (s > kMaxUpdateK) return LOBPCG_ERR_ARG;
   if (work_bytes < update_tc_workspace(n, s, m, slices)) return LOBPCG_ERR_ARG;
   if (beta != 0.0 && beta != 1.0) return LOBPCG_ERR_ARG;
   switch (slices) {

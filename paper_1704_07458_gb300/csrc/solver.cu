@@ -225,10 +225,10 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   h->gwork_bytes = gb;
   if ((rc = dalloc(h, &h->gwork, (size_t)gb))) return rc;
   h->uwork_bytes = mode ? update_ozaki_workspace(n, (int)nsmax, (int)(2 * nx), std::max(sl, 7)) : 0;
-  if (mode == LOBPCG_GEMM_OZAKI_TC)
-    h->uwork_bytes = std::max({h->uwork_bytes,
-                               update_tc_workspace(n, (int)nsmax, (int)(2 * nx), sl),
-                               update_tc_workspace(n, (int)nsmax, (int)(2 * nx), 7)});
+  if (mode == LOBPCG_GEMM_OZAKI_TC)  // the tile split depends on m: take every m
+    for (int m = 1; m <= 2 * nx; ++m)
+      h->uwork_bytes = std::max({h->uwork_bytes, update_tc_workspace(n, (int)nsmax, m, sl),
+                                 update_tc_workspace(n, (int)nsmax, m, 7)});
   if (h->uwork_bytes > 0 && (rc = dalloc(h, &h->uwork, (size_t)h->uwork_bytes))) return rc;
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;

@@ -96,13 +96,21 @@ def test_gram_parity(n, p, q, mode, slices):
     ref = ok.gram(U, V)
     bound = 2 * gamma(n) * (np.abs(U).T @ np.abs(V))
     if mode != gb.LOBPCG_GEMM_F64:
-        # per 64-row chunk c: unit * 64 * max_c|u_i| * max_c|v_j| (2x for the exponent bound)
-        nck = (n + 63) // 64
+        # rows sharing one exponent per column: 64 (mma.sync kernel) or 256
+        # (tcgen05 kernel).  Per block c: unit * len * max_c|u_i| * max_c|v_j|
+        # (2x for the exponent bound)
+        L = 256 if mode == gb.LOBPCG_GEMM_OZAKI_TC else 64
+        nck = (n + L - 1) // L
         mu = np.zeros((nck, p)); mv = np.zeros((nck, q))
         for c in range(nck):
-            mu[c] = np.abs(U[64 * c:64 * c + 64]).max(0)
-            mv[c] = np.abs(V[64 * c:64 * c + 64]).max(0)
-        bound = bound + ozaki_unit(slices) * 64 * 4 * (mu.T @ mv) + 2.0 ** -44 * (np.abs(U).T @ np.abs(V))
+            mu[c] = np.abs(U[L * c:L * c + L]).max(0)
+            mv[c] = np.abs(V[L * c:L * c + L]).max(0)
+        bound = bound + ozaki_unit(slices) * L * 4 * (mu.T @ mv) + 2.0 ** -44 * (np.abs(U).T @ np.abs(V))
+        if mode == gb.LOBPCG_GEMM_OZAKI_TC:
+            # the tcgen05 kernel sums the blocks of a row slab (<= 64 blocks) in
+            # int64 fixed point at the slab's largest exponents: <= 1 unit, i.e.
+            # 2^-44 * 2^(E_i + E_j) <= 2^-42 max|u_i| max|v_j|, lost per block
+            bound = bound + 64 * 2.0 ** -42 * np.outer(np.abs(U).max(0), np.abs(V).max(0))
     assert np.all(np.abs(got - ref) <= bound + 1e-300)
 
 
