@@ -382,7 +382,12 @@ __global__ void __launch_bounds__(256) sign_normalise_kernel(int64_t n, double* 
     }
     __syncthreads();
   }
-  const bool flip = X[si[0] * ldx + j] < 0.0;
+  // decide once: a thread that flips its rows must not change the value the
+  // others read
+  __shared__ int flip_s;
+  if (threadIdx.x == 0) flip_s = X[si[0] * ldx + j] < 0.0 ? 1 : 0;
+  __syncthreads();
+  const bool flip = flip_s != 0;
   if (flip)
     for (int64_t r = threadIdx.x; r < n; r += blockDim.x) X[r * ldx + j] = -X[r * ldx + j];
 }

@@ -49,6 +49,15 @@ def _check_pairs(p, lam, X, be, normA, normB, tol_orth=1e-12):
     assert np.all(np.diff(lam) >= -1e-14)
 
 
+def _same_vector(x, y, atol):
+    a = np.sort(np.abs(y))[::-1]
+    unique_top = a[0] - a[1] > 1e-6 * a[0]
+    if unique_top or np.allclose(x, y, atol=atol):
+        np.testing.assert_allclose(x, y, atol=atol)
+    else:
+        np.testing.assert_allclose(x, -y, atol=atol)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_c1_closed_form_and_oracle(mode):
     p = synth.make_problem("lap2d_32")
@@ -61,9 +70,12 @@ def test_c1_closed_form_and_oracle(mode):
     np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
     np.testing.assert_allclose(st["norm_a"], r.normA, rtol=1e-12)
     _check_pairs(p, lam, X, be, r.normA, r.normB)
-    # non-degenerate pairs: the sign-normalised vectors agree with the oracle
+    # non-degenerate pairs: the vectors agree with the oracle up to sign, and
+    # exactly where the largest-magnitude entry is unique (for x_4 = mode
+    # (2, 2) the largest |entry| is attained at four symmetric points of both
+    # signs, so the sign rule is decided by rounding)
     for i in [0, 3]:
-        np.testing.assert_allclose(X[:, i], r.X[:, i], atol=1e-7)
+        _same_vector(X[:, i], r.X[:, i], 1e-7)
     assert abs(it - r.iters) <= max(3, r.iters // 10)
 
 
