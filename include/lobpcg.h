@@ -40,7 +40,8 @@ typedef enum {
   LOBPCG_ERR_CUDA = 4,           /* a CUDA, cuBLAS or cuSOLVER call failed */
   LOBPCG_ERR_OOM = 5,            /* device allocation failed */
   LOBPCG_ERR_TIMEOUT = 6,        /* wall-clock limit of the options exceeded */
-  LOBPCG_ERR_CALLBACK = 7        /* the preconditioner callback returned non-zero */
+  LOBPCG_ERR_CALLBACK = 7,       /* the preconditioner callback returned non-zero */
+  LOBPCG_ERR_DEGENERATE = 8      /* lobpcg_eig_adjoint: two wanted eigenvalues coincide */
 } lobpcg_status;
 
 typedef enum { LOBPCG_MEM_HOST = 0, LOBPCG_MEM_DEVICE = 1 } lobpcg_mem;
@@ -210,6 +211,38 @@ int lobpcg_residual(int64_t n, const double* X, const double* AX, const double* 
                     int64_t ld, int64_t m, int64_t c0, const double* theta,
                     const double* kdiag, double* W, int64_t ldw, double normA,
                     double normB, double* be, void* stream);
+
+/* Gradients of the eigenpairs with respect to the stored values of A and B.
+ * The paper computes eigenpairs only; this is first-order perturbation theory
+ * of the pencil A x = lambda B x with B-orthonormal, sign-fixed eigenvectors.
+ * For a loss L with upstream gradients glam_i = dL/dlambda_i and
+ * g_i = dL/dx_i of the k pairs (lambda, X) that lobpcg_solve returned for the
+ * handle's current pencil:
+ *   w_i   = sum_{j != i} x_j (x_j^T g_i) / (lambda_i - lambda_j)
+ *         = w_i^in - u_i, w_i^in over the k given pairs, u_i solving
+ *           (A - lambda_i B) u_i = (I - B X X^T) g_i with X^T B u_i = 0 by a
+ *           projected conjugate gradient preconditioned with the handle's K
+ *           (positive definite there when lambda_{k+1} > lambda_k);
+ *   gA[e] = sum_i glam_i x_ri x_ci + (w_ri x_ci + x_ri w_ci) / 2 for each
+ *           stored entry e = (r, c) of A (A_nnz values, A's CSR order);
+ *   gB    = the same with coefficients -lambda_i glam_i - (g_i^T x_i)/2 and
+ *           -lambda_i: B_nnz values on B's CSR pattern, n values for a
+ *           diagonal B; not written (may be NULL) when B = I.
+ * A symmetric pair (r, c), (c, r) is one parameter: its derivative is
+ * gA[(r,c)] + gA[(c,r)].
+ *   lambda (k), X (n x k row-major, leading dimension ldx), glam (k; NULL:
+ *   zero), G (n x k, ldg; NULL: zero, no linear solve): memory kind mem_in.
+ *   gA, gB: memory kind mem_out.  cg_tol (0: 1e-10) is the relative residual
+ *   |r_i| <= cg_tol |(I - B X X^T) g_i| of every column; cg_maxit 0: 20000;
+ *   *cg_iters (host, may be NULL) gets the iterations run.
+ * Returns LOBPCG_ERR_DEGENERATE when two of the k eigenvalues are closer than
+ * 1e-10 max(|lambda|, ||A||) (the eigenvector derivative does not exist),
+ * LOBPCG_ERR_NOT_CONVERGED (outputs written) when cg_maxit is reached.
+ * Allocates its n x k scratch blocks per call; k <= min(n, 2048). */
+int lobpcg_eig_adjoint(lobpcg_t h, int64_t k, const double* lambda, const double* X,
+                       int64_t ldx, const double* glam, const double* G, int64_t ldg,
+                       int mem_in, double* gA, double* gB, int mem_out, double cg_tol,
+                       int32_t cg_maxit, int64_t* cg_iters);
 
 /* Philox4x32-10 normals: Y(r, c) = normal number r*m + c of stream `stream_id`
  * under key `seed` (Box-Muller of two 52-bit uniforms), n x m row-major. */

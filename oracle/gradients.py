@@ -68,8 +68,11 @@ def _gradients(lam, X, W, glam, G):
     return GA, GB
 
 
-def grad_full(A, B, k, glam, G, gap_tol=1e-10):
+def grad_full(A, B, k, glam, G, gap_tol=1e-10, use_jacobi=True):
     """(lambda_k, X_k, dL/dA, dL/dB) with w_i from the full decomposition.
+
+    use_jacobi=False takes the decomposition from LAPACK (the pinned library
+    primitive) for pencils too large for the written-out Jacobi sweeps.
 
     Raises ValueError when two of the k wanted eigenvalues, or lambda_k and
     lambda_{k+1}, are closer than gap_tol * max|lambda| (the eigenvector
@@ -77,17 +80,18 @@ def grad_full(A, B, k, glam, G, gap_tol=1e-10):
     """
     n = A.shape[0]
     lam, X = dense.pencil_eigh(np.asarray(A, float), None if B is None else np.asarray(B, float),
-                               use_jacobi=True)
+                               use_jacobi=use_jacobi)
     X = sign_fix(X)
     scale = np.abs(lam).max()
     gaps = np.diff(lam[:min(k + 1, n)])
     if gaps.size and gaps.min() < gap_tol * scale:
         raise ValueError("degenerate eigenvalues among the wanted pairs")
     W = np.zeros((n, k))
+    XG = X.T @ G  # x_j^T g_i
     for i in range(k):
         for j in range(n):
             if j != i:
-                W[:, i] += X[:, j] * (X[:, j] @ G[:, i]) / (lam[i] - lam[j])
+                W[:, i] += X[:, j] * (XG[j, i] / (lam[i] - lam[j]))
     GA, GB = _gradients(lam, X, W, np.asarray(glam, float), G)
     return lam[:k], X[:, :k], GA, GB
 

@@ -4,7 +4,8 @@ The solver and its kernels live in a CUDA shared library with a C ABI
 (include/lobpcg.h).  This package is only its binding:
 
   _native   one Python function per C entry point, same names (ctypes)
-  Solver    convenience wrapper: create / set_operator / solve / stats
+  Solver    convenience wrapper: create / set_operator / solve / adjoint / stats
+  autograd  LobpcgEig, a torch.autograd.Function over solve and adjoint
 
 PyTorch is used, when present, only to hand device buffers and streams to the
 library.  There is no CPU fallback: if the library is not built, importing the
@@ -16,12 +17,13 @@ from . import _native
 from ._native import (  # noqa: F401
     LOBPCG_OK, LOBPCG_ERR_ARG, LOBPCG_ERR_NOT_CONVERGED, LOBPCG_ERR_BREAKDOWN,
     LOBPCG_ERR_CUDA, LOBPCG_ERR_OOM, LOBPCG_ERR_TIMEOUT, LOBPCG_ERR_CALLBACK,
+    LOBPCG_ERR_DEGENERATE,
     LOBPCG_MEM_HOST, LOBPCG_MEM_DEVICE, LOBPCG_GEMM_F64, LOBPCG_GEMM_OZAKI, LOBPCG_GEMM_OZAKI_TC,
     lobpcg_options_t, lobpcg_stats_t, LobpcgError,
     lobpcg_create, lobpcg_set_operator, lobpcg_set_precond_diag,
     lobpcg_set_precond_callback, lobpcg_solve, lobpcg_get_stats, lobpcg_last_error,
     lobpcg_destroy, lobpcg_spmm, lobpcg_gram, lobpcg_gram_workspace, lobpcg_gram_noalloc,
-    lobpcg_update,
+    lobpcg_update, lobpcg_eig_adjoint,
     lobpcg_residual, lobpcg_philox_normal, load, library_path,
 )
 
@@ -147,6 +149,36 @@ class Solver:
         if rc not in (LOBPCG_OK, LOBPCG_ERR_NOT_CONVERGED) and raise_on_error:
             self._check(rc, "solve")
         return lam, X, it, be, rc
+
+    def adjoint(self, k, lam, X, glam=None, G=None, cg_tol=0.0, cg_maxit=0,
+                raise_on_error=True):
+        """Gradients (gA on A's stored entries, gB) of a loss with upstream
+        gradients glam = dL/dlambda and G = dL/dX at the eigenpairs (lam, X)
+        of the current pencil.  Returns (gA, gB or None, cg_iterations, status).
+        Device tensors in give device tensors out; numpy in gives numpy out."""
+        mem = self._mem(X)
+        n = self.n
+        nnz_a = len(self._keep[2])
+        b_args = self._keep[3]
+        b_len = (len(b_args["B_val"]) if "B_val" in b_args else
+                 (n if b_args.get("B_diag") is not None else 0))
+        if mem == LOBPCG_MEM_DEVICE:
+            import torch
+            gA = torch.empty(nnz_a, dtype=torch.float64, device="cuda")
+            gB = torch.empty(b_len, dtype=torch.float64, device="cuda") if b_len else None
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            lam = np.ascontiguousarray(lam, dtype=np.float64)
+            glam = None if glam is None else np.ascontiguousarray(glam, dtype=np.float64)
+            G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
+            gA = np.empty(nnz_a)
+            gB = np.empty(b_len) if b_len else None
+        rc, its = lobpcg_eig_adjoint(self.h, k, lam, X, X.shape[1], glam, G,
+                                     G.shape[1] if G is not None else 0, mem, gA, gB, mem,
+                                     cg_tol, cg_maxit)
+        if rc not in (LOBPCG_OK, LOBPCG_ERR_NOT_CONVERGED) and raise_on_error:
+            self._check(rc, "adjoint")
+        return gA, gB, its, rc
 
     def stats(self):
         return lobpcg_get_stats(self.h).as_dict()

@@ -16,6 +16,7 @@ LOBPCG_ERR_CUDA = 4
 LOBPCG_ERR_OOM = 5
 LOBPCG_ERR_TIMEOUT = 6
 LOBPCG_ERR_CALLBACK = 7
+LOBPCG_ERR_DEGENERATE = 8
 
 LOBPCG_MEM_HOST = 0
 LOBPCG_MEM_DEVICE = 1
@@ -24,13 +25,15 @@ LOBPCG_GEMM_OZAKI = 1
 LOBPCG_GEMM_OZAKI_TC = 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_CONVERGED", 3: "ERR_BREAKDOWN",
-                4: "ERR_CUDA", 5: "ERR_OOM", 6: "ERR_TIMEOUT", 7: "ERR_CALLBACK"}
+                4: "ERR_CUDA", 5: "ERR_OOM", 6: "ERR_TIMEOUT", 7: "ERR_CALLBACK",
+                8: "ERR_DEGENERATE"}
 
 EXPORTED = [
     "lobpcg_create", "lobpcg_set_operator", "lobpcg_set_precond_diag",
     "lobpcg_set_precond_callback", "lobpcg_solve", "lobpcg_get_stats", "lobpcg_last_error",
     "lobpcg_destroy", "lobpcg_spmm", "lobpcg_gram", "lobpcg_gram_workspace",
     "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
+    "lobpcg_eig_adjoint",
 ]
 
 
@@ -131,6 +134,8 @@ def load(build_if_missing=False):
                                 P]),
         "lobpcg_residual": (I32, [I64, P, P, P, I64, I64, I64, P, P, P, I64, D, D, P, P]),
         "lobpcg_philox_normal": (I32, [I64, I64, ctypes.c_uint64, ctypes.c_uint32, P, I64, P]),
+        "lobpcg_eig_adjoint": (I32, [P, I64, P, P, I64, P, P, I64, I32, P, P, I32, D, I32,
+                                     ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -255,3 +260,13 @@ def lobpcg_residual(n, X, AX, BX, ld, m, c0, theta, kdiag, W, ldw, normA, normB,
 
 def lobpcg_philox_normal(n, m, seed, stream_id, Y, ldy, stream=None):
     return load().lobpcg_philox_normal(n, m, seed, stream_id, ptr(Y), ldy, stream_ptr(stream))
+
+
+def lobpcg_eig_adjoint(h, k, lam, X, ldx, glam, G, ldg, mem_in, gA, gB, mem_out, cg_tol=0.0,
+                       cg_maxit=0):
+    """Gradients of the eigenpairs with respect to the stored values of A and B
+    (see lobpcg.h).  Returns (status, CG iterations)."""
+    it = I64(0)
+    rc = load().lobpcg_eig_adjoint(h, k, ptr(lam), ptr(X), ldx, ptr(glam), ptr(G), ldg, mem_in,
+                                   ptr(gA), ptr(gB), mem_out, cg_tol, cg_maxit, ctypes.byref(it))
+    return rc, it.value

@@ -87,3 +87,34 @@ int sign_normalise(cudaStream_t st, int64_t n, int m, double* X, int64_t ldx, vo
 int64_t sign_normalise_workspace(int64_t n, int m);
 
 }  // namespace lob
+
+namespace lob {
+
+// ---- eigenpair adjoint (adjoint.cu); column reductions use `partial` of
+// adj_reduce_workspace(k) bytes and are fixed-order (deterministic).
+int64_t adj_reduce_workspace(int k);
+// Cin(j, i) = M(j, i) / (lam_i - lam_j) for j != i; *flag = 1 if a gap < gap.
+int adj_coeff(cudaStream_t st, int k, const double* M, int64_t ldm, const double* lam, double gap,
+              double* Cin, int* flag);
+// Q -= (B P) diag(lam) (BP given, or diagonal b, or B = I); out_j = P_j^T Q_j.
+int shift_dot(cudaStream_t st, int64_t n, int k, double* Q, const double* P, const double* BP,
+              const double* b, int64_t ld, const double* lam, double* out, void* partial);
+// alpha = rz/pq: V -= alpha P, R -= alpha Q, Z = R / kdiag (kdiag null: Z = R), rr = |R_j|^2.
+int cg_step(cudaStream_t st, int64_t n, int k, double* V, const double* P, double* R,
+            const double* Q, double* Z, const double* kdiag, int64_t ld, const double* rz,
+            const double* pq, double* rr, void* partial);
+int coldot(cudaStream_t st, int64_t n, int k, const double* X, const double* Y, int64_t ld,
+           double* out, void* partial);
+// P = Z + (rz_new / rz_old) P
+int cg_direction(cudaStream_t st, int64_t n, int k, double* P, const double* Z, int64_t ld,
+                 const double* rz_new, const double* rz_old);
+// coefficient vectors of the A and B gradients (see adjoint.cu)
+int grad_coeff(cudaStream_t st, int k, const double* lam, const double* glam, const double* M,
+               int64_t ldm, double* caA, double* cwA, double* caB, double* cwB);
+int pattern_grad(cudaStream_t st, int64_t n, const int32_t* rowptr, const int32_t* col,
+                 const double* X, const double* W, int64_t ld, int k, const double* ca,
+                 const double* cw, double* out);
+int diag_grad(cudaStream_t st, int64_t n, const double* X, const double* W, int64_t ld, int k,
+              const double* ca, const double* cw, double* out);
+
+}  // namespace lob

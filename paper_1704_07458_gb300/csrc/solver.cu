@@ -742,6 +742,194 @@ int copy_in(lobpcg_ctx* h, void** dst, const void* src, size_t bytes, int mem) {
   return LOBPCG_OK;
 }
 
+
+// ---- eigenpair adjoint: dL/dA, dL/dB from (lambda, X) and dL/dlambda, dL/dX
+// (first-order perturbation theory; see adjoint.cu for the formulas).
+struct DevBuffers {
+  std::vector<void*> p;
+  ~DevBuffers() {
+    for (void* q : p) cudaFree(q);
+  }
+  int get(void** out, size_t bytes) {
+    if (cudaMalloc(out, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return LOBPCG_ERR_OOM;
+    }
+    p.push_back(*out);
+    return LOBPCG_OK;
+  }
+};
+
+int adjoint_impl(lobpcg_ctx* h, int64_t k64, const double* lambda, const double* Xin,
+                 int64_t ldx, const double* glam, const double* Gin, int64_t ldg, int mem_in,
+                 double* gA, double* gB, int mem_out, double cg_tol, int cg_maxit,
+                 int64_t* cg_iters) {
+  const int64_t n = h->n;
+  if (n <= 0) return h->fail(LOBPCG_ERR_ARG, "no operator set");
+  if (k64 <= 0 || k64 > n || k64 > 2048)
+    return h->fail(LOBPCG_ERR_ARG, "k must be in 1..min(n, 2048)");
+  if (!lambda || !Xin || ldx < k64 || !gA) return h->fail(LOBPCG_ERR_ARG, "bad arguments");
+  if (Gin && ldg < k64) return h->fail(LOBPCG_ERR_ARG, "ldg < k");
+  if (h->b_kind != 0 && !gB) return h->fail(LOBPCG_ERR_ARG, "gB is needed when B is not I");
+  if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
+  const int k = (int)k64;
+  if (!(cg_tol > 0)) cg_tol = 1e-10;
+  if (cg_maxit <= 0) cg_maxit = 20000;
+  // the Gram / update scratch of the solver covers every k x k contraction
+  const int64_t nx = std::max<int64_t>(h->ws_nx > 0 ? h->ws_nx : 0, k64);
+  int rc = ensure_workspace(h, nx);
+  if (rc) return h->fail(rc, "workspace allocation failed");
+  const lobpcg_stats_t saved = h->stats;
+  h->timer.st = h->st;
+  h->timer.reset();
+  cudaStream_t st = h->st;
+  const cudaMemcpyKind kin =
+      mem_in == LOBPCG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int64_t ld = round_up(k64, 8);
+  const size_t blk = (size_t)n * ld * sizeof(double), kk = (size_t)k * k * sizeof(double),
+               kv = (size_t)k * sizeof(double);
+  DevBuffers D;
+  double *X, *BX, *F, *Z, *P, *Q, *V, *W, *BP = nullptr;
+  double *M, *Cin, *Gz, *lam, *gl, *rz0, *rz1, *pq, *rr, *caA, *cwA, *caB, *cwB;
+  double *gAd = gA, *gBd = gB;
+  int* flag;
+  void* partial;
+  for (double** b : {&X, &F, &Z, &P, &Q, &V, &W})
+    if ((rc = D.get((void**)b, blk))) return h->fail(rc, "allocation failed");
+  BX = X;
+  if (h->b_kind != 0 && (rc = D.get((void**)&BX, blk))) return h->fail(rc, "allocation failed");
+  if (h->b_kind == 2 && (rc = D.get((void**)&BP, blk))) return h->fail(rc, "allocation failed");
+  for (double** b : {&M, &Cin, &Gz})
+    if ((rc = D.get((void**)b, kk))) return h->fail(rc, "allocation failed");
+  for (double** b : {&lam, &gl, &rz0, &rz1, &pq, &rr, &caA, &cwA, &caB, &cwB})
+    if ((rc = D.get((void**)b, kv))) return h->fail(rc, "allocation failed");
+  if ((rc = D.get((void**)&flag, sizeof(int))) ||
+      (rc = D.get(&partial, (size_t)adj_reduce_workspace(k))))
+    return h->fail(rc, "allocation failed");
+  if (mem_out != LOBPCG_MEM_DEVICE) {
+    if ((rc = D.get((void**)&gAd, (size_t)h->A_nnz * sizeof(double))))
+      return h->fail(rc, "allocation failed");
+    if (h->b_kind && (rc = D.get((void**)&gBd, (size_t)(h->b_kind == 2 ? h->B_nnz : n) *
+                                                   sizeof(double))))
+      return h->fail(rc, "allocation failed");
+  }
+  // inputs
+  LOB_CUDA_OK(cudaMemcpy2DAsync(X, ld * sizeof(double), Xin, ldx * sizeof(double), kv, n, kin, st));
+  LOB_CUDA_OK(cudaMemcpyAsync(lam, lambda, kv, kin, st));
+  if (glam)
+    LOB_CUDA_OK(cudaMemcpyAsync(gl, glam, kv, kin, st));
+  else
+    LOB_CUDA_OK(cudaMemsetAsync(gl, 0, kv, st));
+  if (Gin)
+    LOB_CUDA_OK(cudaMemcpy2DAsync(F, ld * sizeof(double), Gin, ldg * sizeof(double), kv, n, kin,
+                                  st));
+  else
+    LOB_CUDA_OK(cudaMemsetAsync(F, 0, blk, st));
+  LOB_CUDA_OK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  if (h->b_kind == 1 && (rc = diag_scale(st, n, k, h->b_diag, X, ld, BX, ld))) return rc;
+  if (h->b_kind == 2 &&
+      (rc = spmm(st, n, h->B_rp, h->B_ci, h->B_v, X, ld, k, BX, ld, nullptr, nullptr, 0)))
+    return rc;
+  const SegList sX = seg1(X, ld, k), sBX = seg1(BX, ld, k), sF = seg1(F, ld, k),
+                sZ = seg1(Z, ld, k), sV = seg1(V, ld, k);
+  // M = X^T G (g_i^T x_i on its diagonal)
+  if ((rc = gram(h, sX, sF, M, k))) return rc;
+  if ((rc = grad_coeff(st, k, lam, gl, M, k, caA, cwA, caB, cwB))) return rc;
+  int64_t its = 0;
+  bool converged = true;
+  if (Gin) {
+    std::vector<double> lh(k);
+    if ((rc = to_host(h, lh.data(), lam, k))) return rc;
+    double scale = h->stats.norm_a;
+    for (double x : lh) scale = std::max(scale, std::fabs(x));
+    if ((rc = adj_coeff(st, k, M, k, lam, 1e-10 * scale, Cin, flag))) return rc;
+    // F = (I - B X X^T) G
+    if ((rc = update(h, sBX, M, k, k, -1.0, 1.0, sF, out1(F, ld, k), h->zexp))) return rc;
+    std::vector<double> f2(k), r2(k);
+    if ((rc = colsumsq(st, n, F, ld, k, rr, h->rwork))) return rc;
+    if ((rc = to_host(h, f2.data(), rr, k))) return rc;
+    int fl = 0;
+    LOB_CUDA_OK(cudaMemcpyAsync(h->hbuf, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LOB_CUDA_OK(cudaStreamSynchronize(st));
+    memcpy(&fl, h->hbuf, sizeof(int));
+    if (fl) {
+      h->stats = saved;
+      return h->fail(LOBPCG_ERR_DEGENERATE,
+                     "two wanted eigenvalues are closer than 1e-10 max(|lambda|, ||A||)");
+    }
+    const double* kd = (h->k_kind == 0) ? h->adiag : (h->k_kind == 1 ? h->kdiag : nullptr);
+    // project Z onto the B-orthogonal complement of X: Z -= X (BX^T Z)
+    auto project = [&]() -> int {
+      int r;
+      if ((r = gram(h, sBX, sZ, Gz, k))) return r;
+      return update(h, sX, Gz, k, k, -1.0, 1.0, sZ, out1(Z, ld, k), h->zexp);
+    };
+    auto precond = [&]() -> int {
+      if (h->k_kind != 3) return LOBPCG_OK;  // Z = R / kdiag was written by cg_step
+      return h->cb(h->cb_ctx, n, k, F, ld, Z, ld, (void*)st) ? LOBPCG_ERR_CALLBACK : LOBPCG_OK;
+    };
+    // u_0 = 0 (V = -u), R = F; Z = P_B K^-1 R; P = Z
+    LOB_CUDA_OK(cudaMemsetAsync(V, 0, blk, st));
+    LOB_CUDA_OK(cudaMemsetAsync(pq, 0, kv, st));
+    if ((rc = cg_step(st, n, k, V, V, F, F, Z, kd, ld, pq, pq, rr, partial))) return rc;
+    if ((rc = precond())) return h->fail(rc, "preconditioner callback failed");
+    if ((rc = project())) return rc;
+    if ((rc = coldot(st, n, k, F, Z, ld, rz0, partial))) return rc;
+    if ((rc = copy_block(st, n, k, Z, ld, P, ld))) return rc;
+    converged = false;
+    for (int64_t it = 1; it <= cg_maxit; ++it) {
+      if ((rc = spmm(st, n, h->A_rp, h->A_ci, h->A_v, P, ld, k, Q, ld, nullptr, nullptr, 0)))
+        return rc;
+      if (h->b_kind == 2 &&
+          (rc = spmm(st, n, h->B_rp, h->B_ci, h->B_v, P, ld, k, BP, ld, nullptr, nullptr, 0)))
+        return rc;
+      if ((rc = shift_dot(st, n, k, Q, P, BP, h->b_kind == 1 ? h->b_diag : nullptr, ld, lam, pq,
+                          partial)))
+        return rc;
+      if ((rc = cg_step(st, n, k, V, P, F, Q, Z, kd, ld, rz0, pq, rr, partial))) return rc;
+      if ((rc = precond())) return h->fail(rc, "preconditioner callback failed");
+      if ((rc = project())) return rc;
+      if ((rc = coldot(st, n, k, F, Z, ld, rz1, partial))) return rc;
+      if ((rc = cg_direction(st, n, k, P, Z, ld, rz1, rz0))) return rc;
+      std::swap(rz0, rz1);
+      its = it;
+      if (it % 8 == 0 || it == cg_maxit) {
+        if ((rc = to_host(h, r2.data(), rr, k))) return rc;
+        bool all = true;
+        for (int j = 0; j < k; ++j) all = all && !(r2[j] > cg_tol * cg_tol * f2[j]);
+        if (all) {
+          converged = true;
+          break;
+        }
+      }
+    }
+    // W = X Cin - u
+    if ((rc = update(h, sX, Cin, k, k, 1.0, 1.0, sV, out1(W, ld, k), h->zexp))) return rc;
+  } else {
+    LOB_CUDA_OK(cudaMemsetAsync(W, 0, blk, st));
+  }
+  if ((rc = pattern_grad(st, n, h->A_rp, h->A_ci, X, W, ld, k, caA, cwA, gAd))) return rc;
+  if (h->b_kind == 1 && (rc = diag_grad(st, n, X, W, ld, k, caB, cwB, gBd))) return rc;
+  if (h->b_kind == 2 &&
+      (rc = pattern_grad(st, n, h->B_rp, h->B_ci, X, W, ld, k, caB, cwB, gBd)))
+    return rc;
+  if (mem_out != LOBPCG_MEM_DEVICE) {
+    LOB_CUDA_OK(cudaMemcpyAsync(gA, gAd, (size_t)h->A_nnz * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+    if (h->b_kind)
+      LOB_CUDA_OK(cudaMemcpyAsync(gB, gBd,
+                                  (size_t)(h->b_kind == 2 ? h->B_nnz : n) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+  }
+  LOB_CUDA_OK(cudaStreamSynchronize(st));
+  h->timer.flush();
+  h->stats = saved;
+  if (cg_iters) *cg_iters = its;
+  if (!converged)
+    return h->fail(LOBPCG_ERR_NOT_CONVERGED, "adjoint CG reached cg_maxit (outputs written)");
+  return LOBPCG_OK;
+}
+
 }  // namespace
 
 // ============================================================== C ABI
@@ -899,6 +1087,27 @@ LOBPCG_EXPORT int lobpcg_solve(lobpcg_t h, int64_t k, double tol, const double* 
     h->err = std::string("CUDA error: ") + cudaGetErrorString(e);
   } else if (rc && h->err.empty()) {
     h->err = "solve failed";
+  }
+  return rc;
+}
+
+LOBPCG_EXPORT int lobpcg_eig_adjoint(lobpcg_t h, int64_t k, const double* lambda, const double* X,
+                                     int64_t ldx, const double* glam, const double* G,
+                                     int64_t ldg, int mem_in, double* gA, double* gB,
+                                     int mem_out, double cg_tol, int32_t cg_maxit,
+                                     int64_t* cg_iters) {
+  if (!h) return LOBPCG_ERR_ARG;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return h->fail(LOBPCG_ERR_ARG, "handle belongs to another device");
+  h->err.clear();
+  int rc = adjoint_impl(h, k, lambda, X, ldx, glam, G, ldg, mem_in, gA, gB, mem_out, cg_tol,
+                        cg_maxit, cg_iters);
+  if (rc == LOBPCG_ERR_CUDA && h->err.empty()) {
+    cudaError_t e = cudaGetLastError();
+    h->err = std::string("CUDA error: ") + cudaGetErrorString(e);
+  } else if (rc && h->err.empty()) {
+    h->err = "adjoint failed";
   }
   return rc;
 }
