@@ -71,6 +71,9 @@ typedef struct {
   double tau_ortho;       /* 0: 100 eps; Algorithm 5 orthogonality tolerance */
   double tau_skip;        /* 0: 100 eps; switch to orthogonalisation when cond(R)^-3 < tau_skip (Sec. 5.3) */
   double max_seconds;     /* 0: no limit; host wall-clock limit -> LOBPCG_ERR_TIMEOUT */
+  int32_t dense_eig;      /* eigensolver of the projected matrices: 0 FP32 decomposition
+                             refined to FP64 (Ogita-Aishima steps, cluster Jacobi), 1 FP64
+                             syevd (cuSOLVER) */
 } lobpcg_options_t;
 
 /* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
@@ -101,6 +104,9 @@ typedef struct {
   /* BF16 tensor-core work of the emulated contractions: the FP64-equivalent
    * flops times the S(S+1)/2 digit pairs of an S-slice split (0 in FP64 mode) */
   double gram_tensor_flops, update_tensor_flops;
+  /* projected eigenproblems solved, and how many of them fell back to the
+   * FP64 syevd (FP32 stage failed or a cluster wider than 32) */
+  int64_t eig_calls, eig_fallbacks;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.

@@ -50,6 +50,7 @@ class lobpcg_options_t(ctypes.Structure):
         ("tau_ortho", ctypes.c_double),
         ("tau_skip", ctypes.c_double),
         ("max_seconds", ctypes.c_double),
+        ("dense_eig", ctypes.c_int32),
     ]
 
 
@@ -82,6 +83,8 @@ class lobpcg_stats_t(ctypes.Structure):
         ("update_flops", ctypes.c_double),
         ("gram_tensor_flops", ctypes.c_double),
         ("update_tensor_flops", ctypes.c_double),
+        ("eig_calls", ctypes.c_int64),
+        ("eig_fallbacks", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -40,6 +40,13 @@ __global__ void scale_sym_kernel(int n, const double* G, int ldg, const double* 
   M[i + (int64_t)j * ldm] = d[i] * (0.5 * (gij + gji)) * d[j];
 }
 
+__global__ void set_identity_kernel(int n, double* A, int lda) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  A[i + (int64_t)j * lda] = i == j ? 1.0 : 0.0;
+}
+
 __global__ void copy_mat_kernel(int rows, int cols, const double* S, int lds, double* D,
                                 int ldd) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,107 +129,336 @@ __global__ void small_stats_kernel(const double* G, int rows, int cols, int ldg,
   }
 }
 
-// cond(R) = sqrt(lambda_max(M) / lambda_min(M)) for M = R^T R (R upper, from
-// potrf), estimated in one CTA: power iterations for lambda_max(M) and for
-// lambda_max(M^-1) = 1/lambda_min(M), the latter through the two triangular
-// solves with R.  FP32 arithmetic: the value only feeds the order-of-
-// magnitude test cond(R)^-3 < tau_skip.  R is staged in shared memory when it
-// fits (rstage != 0).  out[0] = cond estimate.
+// cond(R) = sqrt(lambda_max(M) lambda_max(R^-1 R^-T)) for M = R^T R, from
+// power iterations with the explicit inverse Rinv (one CTA, matrix-vector
+// products only: every product is parallel over rows or columns).  The value
+// feeds the order-of-magnitude test cond(R)^-3 < tau_skip, so the iterations
+// run in FP32 on FP64 data.  out[0] = cond estimate (inf when Rinv or M gives
+// a non-finite or non-positive value).
 constexpr int kCondIters = 8;
+constexpr int kCondThreads = 1024;
 
-__global__ void __launch_bounds__(256) cond_estimate_kernel(int n, const double* M, int ldm,
-                                                            const double* R, int ldr, int rstage,
-                                                            double* out) {
+__global__ void __launch_bounds__(kCondThreads) cond_estimate_kernel(int n, const double* M,
+                                                                     int ldm, const double* Ri,
+                                                                     int ldr, double* out) {
   extern __shared__ float sh[];
   float* x = sh;          // n
   float* y = sh + n;      // n
-  float* Rs = sh + 2 * n; // n x n (column-major) when staged
-  __shared__ float red[256];
-  __shared__ float lmax_s;
-  const int tid = threadIdx.x;
-  auto block_sum = [&](float v) -> float {
-    red[tid] = v;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) red[tid] += red[tid + s];
-      __syncthreads();
+  float* z = sh + 2 * n;  // n
+  __shared__ float red[3][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kCondThreads / 32;
+  auto block_sum3 = [&](float a, float b, float c, float& ra, float& rb, float& rc) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    const float r = red[0];
-    __syncthreads();
-    return r;
-  };
-  if (rstage)
-    for (int64_t e = tid; e < (int64_t)n * n; e += 256) {
-      const int i = (int)(e % n), j = (int)(e / n);
-      Rs[e] = i <= j ? (float)R[i + (int64_t)j * ldr] : 0.f;
+    if (lane == 0) {
+      red[0][warp] = a;
+      red[1][warp] = b;
+      red[2][warp] = c;
     }
-  auto Rij = [&](int i, int j) -> float {
-    return rstage ? Rs[i + (int64_t)j * n] : (float)R[i + (int64_t)j * ldr];
+    __syncthreads();
+    ra = rb = rc = 0.f;
+    for (int w = 0; w < nw; ++w) {
+      ra += red[0][w];
+      rb += red[1][w];
+      rc += red[2][w];
+    }
+    __syncthreads();
   };
-  // lambda_max(M)
-  for (int i = tid; i < n; i += 256) x[i] = 1.0f + 0.001f * (float)(i % 7);
-  __syncthreads();
-  float lam = 1.0f;
-  for (int it = 0; it < kCondIters; ++it) {
-    for (int i = tid; i < n; i += 256) {
+  // column-oriented product: y_i = sum_j A(j, i) x_j (warp per column i)
+  auto colprod = [&](const double* A, int lda, bool upper_only, const float* in, float* outv) {
+    for (int i = warp; i < n; i += nw) {
       float s = 0.f;
-      for (int j = 0; j < n; ++j) s += (float)M[i + (int64_t)j * ldm] * x[j];
-      y[i] = s;
+      const int jmax = upper_only ? i + 1 : n;
+      for (int j = lane; j < jmax; j += 32) s += (float)A[j + (int64_t)i * lda] * in[j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) outv[i] = s;
     }
     __syncthreads();
-    float nx = 0.f, ny = 0.f, nn = 0.f;
-    for (int i = tid; i < n; i += 256) {
-      nx += x[i] * y[i];
-      ny += y[i] * y[i];
-      nn += x[i] * x[i];
+  };
+  // row-oriented product with the upper triangle: y_i = sum_{j >= i} A(i, j) x_j
+  auto rowprod_upper = [&](const double* A, int lda, const float* in, float* outv) {
+    for (int i = tid; i < n; i += kCondThreads) {
+      float s = 0.f;
+      for (int j = i; j < n; ++j) s += (float)A[i + (int64_t)j * lda] * in[j];
+      outv[i] = s;
     }
-    const float xy = block_sum(nx), yy = block_sum(ny), xx = block_sum(nn);
-    if (xx > 0.f) lam = fmaxf(lam, xy / xx);  // Rayleigh quotient
-    const float inv = yy > 0.f ? rsqrtf(yy) : 0.f;
-    for (int i = tid; i < n; i += 256) x[i] = y[i] * inv;
     __syncthreads();
+  };
+  auto power = [&](int which) -> float {  // 0: M (symmetric), 1: Rinv Rinv^T
+    for (int i = tid; i < n; i += kCondThreads) x[i] = 1.0f + 0.001f * (float)(i % 7);
+    __syncthreads();
+    float lam = 0.f;
+    for (int it = 0; it < kCondIters; ++it) {
+      float* res = y;
+      if (which == 0) {
+        colprod(M, ldm, false, x, y);
+      } else {
+        colprod(Ri, ldr, true, x, y);  // y = Rinv^T x (Rinv upper: column i has rows <= i)
+        rowprod_upper(Ri, ldr, y, z);  // z = Rinv y
+        res = z;
+      }
+      float a = 0.f, b = 0.f, c = 0.f;
+      for (int i = tid; i < n; i += kCondThreads) {
+        a += x[i] * res[i];
+        b += res[i] * res[i];
+        c += x[i] * x[i];
+      }
+      float xy, yy, xx;
+      block_sum3(a, b, c, xy, yy, xx);
+      if (!(yy > 0.f) || !isfinite(yy)) return INFINITY;
+      if (xx > 0.f) lam = fmaxf(lam, xy / xx);
+      const float inv = rsqrtf(yy);
+      for (int i = tid; i < n; i += kCondThreads) x[i] = res[i] * inv;
+      __syncthreads();
+    }
+    return lam;
+  };
+  const float lmax = power(0);
+  const float imax = power(1);
+  if (tid == 0)
+    out[0] = (isfinite(lmax) && isfinite(imax) && lmax > 0.f && imax > 0.f)
+                 ? sqrt((double)lmax * (double)imax)
+                 : INFINITY;
+}
+
+
+// ------------------------------------------------------------ eigensolver
+// Symmetric eigendecomposition of the small projected matrices, designed for
+// a part whose FP64 rate is 1/64 of its FP32 rate: cuSOLVER's FP32 syevd gives
+// X0 (about 1e-7 accurate); two steps of the refinement of Ogita and Aishima
+// ("Iterative refinement for symmetric eigenvalue decomposition", Japan J.
+// Indust. Appl. Math. 35, 2018) in FP64 GEMMs bring every eigenpair whose
+// eigenvalue is separated by more than delta to FP64 accuracy; eigenvalues
+// closer than delta form clusters whose FP64 block of X^T A X is
+// diagonalised by Jacobi rotations; a Newton-Schulz step before that restores
+// orthonormality to rounding level.  One host read (the Rayleigh quotients,
+// delta) per call.
+//
+// One refinement step for X ~ eigenvectors of A (n x n, column-major):
+//   G = X^T X, R = I - G, S = X^T A X, d_i = s_ii / g_ii,
+//   delta = 2 (||S - diag(d)||_F + ||A||_F ||R||_F),
+//   E_ij = (s_ij + d_j r_ij) / (d_j - d_i) if |d_i - d_j| > delta, else r_ij / 2,
+//   X <- X + X E,
+// from X' = X (I + E) with X'^T X' = I and X'^T A X' diagonal to first order
+// (E + E^T = R, E^T D + D E = D - S off the diagonal).
+
+constexpr int kRefineSteps = 2;
+constexpr int kRefBlocks = 64;
+constexpr int kMaxRun = 32;  // cluster blocks up to this size: Jacobi in shared memory
+
+// A <- (A + A^T) / 2 in place (threads of the strict lower triangle)
+__global__ void symmetrize_kernel(int n, double* A, int lda) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  if (i <= j) return;
+  const double v = 0.5 * (A[i + (int64_t)j * lda] + A[j + (int64_t)i * lda]);
+  A[i + (int64_t)j * lda] = v;
+  A[j + (int64_t)i * lda] = v;
+}
+
+__global__ void to_f32_kernel(int64_t total, const double* __restrict__ A, float* __restrict__ B) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < total) B[e] = (float)A[e];
+}
+__global__ void to_f64_kernel(int64_t total, const float* __restrict__ A, double* __restrict__ B) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < total) B[e] = (double)A[e];
+}
+
+// partial[b] = (||S - diag(d)||_F^2, ||R||_F^2, ||A||_F^2) over block b's elements
+__global__ void __launch_bounds__(256) oa_norms_kernel(int n, const double* __restrict__ S,
+                                                       const double* __restrict__ G,
+                                                       const double* __restrict__ A, int lda,
+                                                       double* __restrict__ partial) {
+  __shared__ double red[3][256];
+  double a = 0.0, b = 0.0, c = 0.0;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const double s = S[e], g = G[e];
+    const double aij = A[i + (int64_t)j * lda];
+    if (i == j) {
+      const double d = g != 0.0 ? s / g : s;
+      a = fma(s - d, s - d, a);
+      b = fma(1.0 - g, 1.0 - g, b);
+    } else {
+      a = fma(s, s, a);
+      b = fma(g, g, b);
+    }
+    c = fma(aij, aij, c);
   }
-  if (tid == 0) lmax_s = lam;
-  // lambda_max(M^-1) by x <- R^-1 R^-T x
-  for (int i = tid; i < n; i += 256) x[i] = 1.0f - 0.002f * (float)(i % 5);
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
   __syncthreads();
-  float mu = 0.f;
-  bool bad = false;
-  for (int it = 0; it < kCondIters && !bad; ++it) {
-    // y = R^-T x: forward substitution, column-oriented (R^T lower)
-    for (int i = tid; i < n; i += 256) y[i] = x[i];
-    __syncthreads();
-    for (int i = 0; i < n; ++i) {
-      const float yi = y[i] / Rij(i, i);
-      __syncthreads();
-      for (int j = i + 1 + tid; j < n; j += 256) y[j] -= Rij(i, j) * yi;
-      if (tid == 0) y[i] = yi;
-      __syncthreads();
-    }
-    // x = R^-1 y: back substitution, column-oriented
-    for (int i = n - 1; i >= 0; --i) {
-      const float yi = y[i] / Rij(i, i);
-      __syncthreads();
-      for (int j = tid; j < i; j += 256) y[j] -= Rij(j, i) * yi;
-      if (tid == 0) y[i] = yi;
-      __syncthreads();
-    }
-    float a = 0.f, b = 0.f, c = 0.f;
-    for (int i = tid; i < n; i += 256) {
-      a += x[i] * y[i];
-      b += y[i] * y[i];
-      c += x[i] * x[i];
-    }
-    const float xy = block_sum(a), yy = block_sum(b), xx = block_sum(c);
-    if (!(yy > 0.f) || !isfinite(yy)) bad = true;
-    if (xx > 0.f) mu = fmaxf(mu, xy / xx);
-    const float inv = (yy > 0.f && isfinite(yy)) ? rsqrtf(yy) : 0.f;
-    for (int i = tid; i < n; i += 256) x[i] = y[i] * inv;
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int t = 0; t < 3; ++t) red[t][threadIdx.x] += red[t][threadIdx.x + w];
     __syncthreads();
   }
-  if (tid == 0) {
-    const double lmin = (bad || !(mu > 0.f)) ? 0.0 : 1.0 / (double)mu;
-    out[0] = lmin > 0.0 ? sqrt((double)lmax_s / lmin) : INFINITY;
+  if (threadIdx.x == 0)
+    for (int t = 0; t < 3; ++t) partial[blockIdx.x * 3 + t] = red[t][0];
+}
+
+// E from S, G and delta (every block reduces the partials itself); block 0
+// stores delta.
+__global__ void __launch_bounds__(256) oa_update_kernel(int n, const double* __restrict__ S,
+                                                        const double* __restrict__ G,
+                                                        const double* __restrict__ partial,
+                                                        int nparts, double* __restrict__ E,
+                                                        double* __restrict__ delta_out) {
+  __shared__ double dl;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      a += partial[3 * p];
+      b += partial[3 * p + 1];
+      c += partial[3 * p + 2];
+    }
+    dl = 2.0 * (sqrt(a) + sqrt(c) * sqrt(b));
+    if (blockIdx.x == 0) *delta_out = dl;
+  }
+  __syncthreads();
+  const double delta = dl;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const double g = G[e];
+    double out;
+    if (i == j) {
+      out = 0.5 * (1.0 - g);
+    } else {
+      const double gi = G[i + (int64_t)i * n], gj = G[j + (int64_t)j * n];
+      const double di = S[i + (int64_t)i * n] / gi, dj = S[j + (int64_t)j * n] / gj;
+      const double r = -g;
+      if (fabs(di - dj) > delta)
+        out = (S[e] + dj * r) / (dj - di);
+      else
+        out = 0.5 * r;
+    }
+    E[e] = out;
+  }
+}
+
+// G <- 3/2 I - 1/2 G: X (3/2 I - 1/2 X^T X) squares the orthogonality error
+// of X (one Newton-Schulz step towards the orthogonal polar factor)
+__global__ void newton_schulz_kernel(int n, double* G) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+}
+
+__global__ void diag_extract_kernel(int n, const double* __restrict__ S, const double* delta,
+                                    double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = S[i + (int64_t)i * n];
+  if (i == n) out[n] = *delta;
+}
+
+// Xo(:, k) = X(:, perm[k]); lam[k] = S(perm[k], perm[k])
+__global__ void permute_cols_kernel(int n, const double* __restrict__ X,
+                                    const double* __restrict__ S, const int* __restrict__ perm,
+                                    double* __restrict__ Xo, int ldo, double* __restrict__ lam) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int r = (int)(e % n), k = (int)(e / n);
+  const int p = perm[k];
+  Xo[r + (int64_t)k * ldo] = X[r + (int64_t)p * n];
+  if (r == 0) lam[k] = S[p + (int64_t)p * n];
+}
+
+// One block per cluster run [a, a + m) of the permuted order: cyclic Jacobi on
+// the FP64 block S(perm[a + i], perm[a + j]) by one warp, eigenvalues sorted
+// ascending, then Xo(:, a : a + m) <- Xo(:, a : a + m) Q by all threads.
+__global__ void __launch_bounds__(256) cluster_jacobi_kernel(int n, const double* __restrict__ S,
+                                                             const int* __restrict__ perm,
+                                                             const int* __restrict__ runs,
+                                                             double* __restrict__ Xo, int ldo,
+                                                             double* __restrict__ lam) {
+  __shared__ double M[kMaxRun][kMaxRun + 1], Q[kMaxRun][kMaxRun + 1];
+  __shared__ double ev[kMaxRun];
+  __shared__ int order[kMaxRun];
+  const int a = runs[2 * blockIdx.x], m = runs[2 * blockIdx.x + 1];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    const double sij = S[perm[a + i] + (int64_t)perm[a + j] * n];
+    const double sji = S[perm[a + j] + (int64_t)perm[a + i] * n];
+    M[i][j] = 0.5 * (sij + sji);
+    Q[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int e = lane; e < m * m; e += 32) {
+        const int i = e % m, j = e / m;
+        const double v = M[i][j] * M[i][j];
+        tot += v;
+        if (i != j) off += v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if (!(off > 1e-30 * tot)) break;
+      for (int p = 0; p < m - 1; ++p)
+        for (int q = p + 1; q < m; ++q) {
+          const double apq = M[p][q];
+          if (apq == 0.0) continue;
+          // rotation zeroing M[p][q] (Golub & Van Loan, Sec. 8.5.2)
+          const double tau = (M[q][q] - M[p][p]) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+          __syncwarp();
+          for (int k = lane; k < m; k += 32) {  // columns p, q
+            const double mkp = M[k][p], mkq = M[k][q];
+            M[k][p] = c * mkp - s * mkq;
+            M[k][q] = s * mkp + c * mkq;
+            const double qkp = Q[k][p], qkq = Q[k][q];
+            Q[k][p] = c * qkp - s * qkq;
+            Q[k][q] = s * qkp + c * qkq;
+          }
+          __syncwarp();
+          for (int k = lane; k < m; k += 32) {  // rows p, q
+            const double mpk = M[p][k], mqk = M[q][k];
+            M[p][k] = c * mpk - s * mqk;
+            M[q][k] = s * mpk + c * mqk;
+          }
+          __syncwarp();
+        }
+    }
+    if (lane == 0) {  // ascending order of the eigenvalues (insertion sort, m <= 32)
+      for (int i = 0; i < m; ++i) {
+        ev[i] = M[i][i];
+        order[i] = i;
+      }
+      for (int i = 1; i < m; ++i)
+        for (int j = i; j > 0 && ev[order[j]] < ev[order[j - 1]]; --j) {
+          const int t = order[j];
+          order[j] = order[j - 1];
+          order[j - 1] = t;
+        }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += blockDim.x) lam[a + i] = ev[order[i]];
+  for (int r = tid; r < n; r += blockDim.x) {
+    double x[kMaxRun];
+    for (int j = 0; j < m; ++j) x[j] = Xo[r + (int64_t)(a + j) * ldo];
+    for (int i = 0; i < m; ++i) {
+      const int c = order[i];
+      double v = 0.0;
+      for (int j = 0; j < m; ++j) v = fma(x[j], Q[j][c], v);
+      Xo[r + (int64_t)(a + i) * ldo] = v;
+    }
   }
 }
 
@@ -261,9 +497,105 @@ static int dscale(DenseLayer& L, int n, const double* G, int ldg, double* M, int
   return LOBPCG_OK;
 }
 
-static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
+static int syevd_f64(DenseLayer& L, bool vectors, int n, double* A, int lda) {
   SOL_OK(cusolverDnDsyevd(L.sol, vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR,
                           CUBLAS_FILL_MODE_LOWER, n, A, lda, L.ev, L.work, L.lwork, L.info));
+  return LOBPCG_OK;
+}
+
+// Eigenvalues ascending into L.ev, eigenvectors into A (column-major, lda =
+// n), by the FP32 decomposition + FP64 refinement above (eig_mode 0) or
+// cuSOLVER's FP64 syevd (eig_mode 1, and the fallback when the FP32 stage
+// fails, meets a non-finite value or a cluster wider than kMaxRun).
+static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
+  if (L.eig_mode == 1 || n < 2 || lda != n) return syevd_f64(L, vectors, n, A, lda);
+  const int64_t nn = (int64_t)n * n;
+  const double one = 1.0, zero = 0.0;
+  ++L.eig_calls;
+  symmetrize_kernel<<<blocks_for(nn), 256, 0, L.st>>>(n, A, lda);
+  LAUNCH_OK(L);
+  to_f32_kernel<<<blocks_for(nn), 256, 0, L.st>>>(nn, A, L.Af);
+  LAUNCH_OK(L);
+  SOL_OK(cusolverDnSsyevd(L.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, L.Af, n,
+                          L.wf, L.swork, L.lswork, L.info));
+  double* X = L.R[0];
+  double* X1 = L.R[1];
+  double* AX = L.R[2];
+  double* S = L.R[3];
+  double* G = L.R[4];
+  double* E = L.R[5];
+  to_f64_kernel<<<blocks_for(nn), 256, 0, L.st>>>(nn, L.Af, X);
+  LAUNCH_OK(L);
+  const int nb = (int)std::min<int64_t>(kRefBlocks, ceil_div(nn, 256));
+  for (int step = 0; step < kRefineSteps; ++step) {
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, A, lda, X, n, &zero, AX,
+                        n));
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, X, n, AX, n, &zero, S,
+                        n));
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, X, n, X, n, &zero, G,
+                        n));
+    oa_norms_kernel<<<nb, 256, 0, L.st>>>(n, S, G, A, lda, L.part);
+    LAUNCH_OK(L);
+    oa_update_kernel<<<(unsigned)std::min<int64_t>(4 * 152, ceil_div(nn, 256)), 256, 0, L.st>>>(
+        n, S, G, L.part, nb, E, L.scal + 8);
+    LAUNCH_OK(L);
+    LOB_CUDA_OK(cudaMemcpyAsync(X1, X, nn * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, X, n, E, n, &one, X1,
+                        n));
+    std::swap(X, X1);
+  }
+  // the steps leave X^T X - I near 1e-13; one Newton-Schulz step restores
+  // orthonormality to rounding level
+  BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, X, n, X, n, &zero, G, n));
+  newton_schulz_kernel<<<blocks_for(nn), 256, 0, L.st>>>(n, G);
+  LAUNCH_OK(L);
+  BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, X, n, G, n, &zero, X1, n));
+  std::swap(X, X1);
+  BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, A, lda, X, n, &zero, AX,
+                      n));
+  BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, X, n, AX, n, &zero, S, n));
+  diag_extract_kernel<<<blocks_for(n + 1), 256, 0, L.st>>>(n, S, L.scal + 8, L.ev);
+  LAUNCH_OK(L);
+  LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.ev, (n + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                              L.st));
+  LOB_CUDA_OK(cudaMemcpyAsync(L.host + n + 1, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  int info;
+  memcpy(&info, L.host + n + 1, sizeof(int));
+  const double* d = L.host;
+  const double delta = d[n];
+  bool ok = info == 0 && std::isfinite(delta);
+  for (int i = 0; ok && i < n; ++i) ok = std::isfinite(d[i]);
+  int* perm = L.hint;
+  int* runs = L.hint + n;
+  int nruns = 0;
+  if (ok) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    std::sort(perm, perm + n, [&](int a, int b) { return d[a] < d[b] || (d[a] == d[b] && a < b); });
+    for (int k = 0; k < n && ok;) {
+      int e = k + 1;
+      while (e < n && d[perm[e]] - d[perm[e - 1]] <= delta) ++e;
+      if (e - k > kMaxRun) ok = false;
+      if (e - k >= 2) {
+        runs[2 * nruns] = k;
+        runs[2 * nruns + 1] = e - k;
+        ++nruns;
+      }
+      k = e;
+    }
+  }
+  if (!ok) {
+    ++L.eig_fallbacks;
+    return syevd_f64(L, vectors, n, A, lda);
+  }
+  LOB_CUDA_OK(cudaMemcpyAsync(L.dint, L.hint, (size_t)(n + 2 * nruns) * sizeof(int),
+                              cudaMemcpyHostToDevice, L.st));
+  permute_cols_kernel<<<blocks_for(nn), 256, 0, L.st>>>(n, X, S, L.dint, A, lda, L.ev);
+  LAUNCH_OK(L);
+  if (nruns > 0) {
+    cluster_jacobi_kernel<<<nruns, 256, 0, L.st>>>(n, S, L.dint, L.dint + n, A, lda, L.ev);
+    LAUNCH_OK(L);
+  }
   return LOBPCG_OK;
 }
 
@@ -286,12 +618,26 @@ int DenseLayer::init(cudaStream_t stream, int64_t n_max) {
   const size_t mat = (size_t)nmax * nmax * sizeof(double);
   for (auto& a : A)
     if (cudaMalloc(&a, mat) != cudaSuccess) return LOBPCG_ERR_OOM;
-  if (cudaMalloc(&ev, nmax * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&ev, (nmax + 8) * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&d, nmax * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&tau, nmax * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&scal, 16 * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&info, 4 * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMallocHost(&host, (nmax + 64) * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  for (auto& r : R)
+    if (cudaMalloc(&r, mat) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&Af, (size_t)nmax * nmax * sizeof(float)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&wf, nmax * sizeof(float)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&part, 3 * kRefBlocks * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&dint, 3 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMallocHost(&hint, 3 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  {
+    int lws = 0;
+    SOL_OK(cusolverDnSsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                       (int)nmax, Af, (int)nmax, wf, &lws));
+    lswork = std::max(lws, 1);
+    if (cudaMalloc(&swork, (size_t)lswork * sizeof(float)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  }
   const int n = (int)nmax;
   int lw = 0, best = 0;
   SOL_OK(cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
@@ -322,6 +668,19 @@ void DenseLayer::release() {
   if (work) cudaFree(work);
   if (host) cudaFreeHost(host);
   ev = d = tau = scal = work = host = nullptr;
+  for (auto& r : R) {
+    if (r) cudaFree(r);
+    r = nullptr;
+  }
+  if (Af) cudaFree(Af);
+  if (wf) cudaFree(wf);
+  if (swork) cudaFree(swork);
+  if (part) cudaFree(part);
+  if (dint) cudaFree(dint);
+  if (hint) cudaFreeHost(hint);
+  Af = wf = swork = nullptr;
+  part = nullptr;
+  dint = hint = nullptr;
   info = nullptr;
   if (sol) cusolverDnDestroy(sol);
   if (blas) cublasDestroy(blas);
@@ -401,18 +760,22 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
       *condR = INFINITY;
       return LOBPCG_OK;
     }
+    // Rinv = R^-1 (one triangular solve with the identity), then cond(R) from
+    // power iterations on M = R^T R (still in Tz) and on Rinv Rinv^T
+    set_identity_kernel<<<blocks_for((int64_t)ns * ns), 256, 0, L.st>>>(ns, Q2, ld);
+    LAUNCH_OK(L);
+    BLAS_OK(cublasDtrsm(L.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                        CUBLAS_DIAG_NON_UNIT, ns, ns, &one, Rm, ld, Q2, ld));
     {
-      // stage R in shared memory when it fits (227 KB per block)
-      const size_t full = (size_t)(2 * ns + (size_t)ns * ns) * sizeof(float);
-      const int rstage = full <= 200 * 1024 ? 1 : 0;
-      const size_t bytes = rstage ? full : 2 * ns * sizeof(float);
+      const size_t bytes = 3 * (size_t)ns * sizeof(float);
       static bool configured = false;
       if (!configured) {
         LOB_CUDA_OK(cudaFuncSetAttribute(cond_estimate_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         configured = true;
       }
-      cond_estimate_kernel<<<1, 256, bytes, L.st>>>(ns, Tz, ld, Rm, ld, rstage, L.scal);
+      if (bytes > 200 * 1024) return LOBPCG_ERR_ARG;
+      cond_estimate_kernel<<<1, kCondThreads, bytes, L.st>>>(ns, Tz, ld, Q2, ld, L.scal);
       LAUNCH_OK(L);
     }
     double cr;
@@ -422,14 +785,14 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
       *flip = true;
       return LOBPCG_OK;
     }
-    BLAS_OK(cublasDtrsm(L.blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                        CUBLAS_DIAG_NON_UNIT, ns, ns, &one, Rm, ld, H, ld));
-    BLAS_OK(cublasDtrsm(L.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T,
-                        CUBLAS_DIAG_NON_UNIT, ns, ns, &one, Rm, ld, H, ld));
+    // H <- Rinv^T H Rinv (two GEMMs through M), eig, T Z = D Rinv Z
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, ns, ns, ns, &one, H, ld, Q2, ld, &zero,
+                        M, ld));
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, ns, ns, ns, &one, Q2, ld, M, ld, &zero,
+                        H, ld));
     if ((rc = syevd(L, true, ns, H, ld))) return rc;
-    if ((rc = copy_mat(L, ns, ns, H, ld, Tz, ld))) return rc;
-    BLAS_OK(cublasDtrsm(L.blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                        CUBLAS_DIAG_NON_UNIT, ns, ns, &one, Rm, ld, Tz, ld));
+    BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, ns, ns, ns, &one, Q2, ld, H, ld, &zero,
+                        Tz, ld));
     scale_rows_kernel<<<blocks_for((int64_t)ns * ns), 256, 0, L.st>>>(ns, ns, L.d, Tz, ld);
     LAUNCH_OK(L);
   }

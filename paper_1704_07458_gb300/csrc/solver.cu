@@ -233,6 +233,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
   if ((rc = h->dense.init(h->st, nsmax))) return rc;
+  h->dense.eig_mode = h->opt.dense_eig == 1 ? 1 : 0;
   h->ws_n = n;
   h->ws_nx = nx;
   h->ws_b = h->b_kind;
@@ -443,6 +444,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   if (rc) return h->fail(rc, "workspace allocation failed");
   const auto t_start = std::chrono::steady_clock::now();
   const int64_t launches0 = g_launches;
+  const int64_t eig0 = h->dense.eig_calls, eigf0 = h->dense.eig_fallbacks;
   h->timer.st = h->st;
   h->timer.reset();
   h->timer.mark();
@@ -706,6 +708,8 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.iterations = it;
   h->stats.converged = nc;
   h->stats.gpu_launches = g_launches - launches0;
+  h->stats.eig_calls = h->dense.eig_calls - eig0;
+  h->stats.eig_fallbacks = h->dense.eig_fallbacks - eigf0;
   h->stats.ms_spmm = h->timer.total[PH_SPMM];
   h->stats.ms_gram = h->timer.total[PH_GRAM];
   h->stats.ms_update = h->timer.total[PH_UPDATE];

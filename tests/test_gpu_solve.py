@@ -228,3 +228,21 @@ def test_c2_full_size_properties(mode):
     # the pencil's spectrum lies between the Laplacian's divided by 2 and by 1
     lap = synth.problems.closed_form_laplacian((64, 64, 64), 64)
     assert np.all(lam >= lap / 2.0 - 1e-12) and np.all(lam <= lap + 1e-12)
+
+
+@pytest.mark.parametrize("dense_eig", [0, 1])
+def test_projected_eigensolver_forms_agree(dense_eig):
+    """The FP32-decomposition + FP64-refinement eigensolver of the projected
+    pencils (dense_eig 0) and cuSOLVER's FP64 syevd (1) give the same pairs."""
+    p = synth.make_problem("lap3d_64_diagB", N=16, k=16)
+    nx = synth.block_width(p.k)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, nx)
+    lam, X, it, be, rc, st = _gpu(p, X0=X0, mode="f64", dense_eig=dense_eig)
+    assert rc == 0
+    if dense_eig == 0:
+        assert st["eig_calls"] >= st["iterations"] and st["eig_fallbacks"] == 0
+    else:
+        assert st["eig_calls"] == 0
+    _, r = _oracle(p)
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    _check_pairs(p, lam, X, be, r.normA, r.normB)
