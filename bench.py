@@ -150,6 +150,7 @@ def workload_config(args, p):
     return {"workload": f"{args.workload}: {p.note}, n={p.n}, nnz={p.A.nnz}, k={p.k}, "
                         f"tol={p.tol}", "n": p.n, "nnz": p.A.nnz, "k": p.k, "tol": p.tol,
             "block_width": None, "gemm_mode": args.mode,
+            "dense_eig": "fp64_syevd" if getattr(args, "dense_eig", 0) == 0 else "fp32_refined",
             "l2": "working set > L2 (15 blocks of n x 72 doubles, 151 MB each); no flush",
             "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "1gpu"}
 
@@ -168,6 +169,9 @@ def main():
                     help="cap the iterations of every solve (0: the solver's default of 2000); "
                          "a capped run is a bounded profile of the same step, not a bench value")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dense-eig", type=int, default=0, choices=[0, 1],
+                    help="eigensolver of the projected pencils: 0 FP64 syevd, 1 FP32 refined "
+                         "to FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -190,7 +194,8 @@ def main():
     A_rp, A_ci, A_v = dev(p.A.rowptr), dev(p.A.col), dev(p.A.val)
     bd = dev(p.b_diag) if p.b_diag is not None else None
 
-    solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit)
+    solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit,
+                       dense_eig=args.dense_eig)
     solver.set_operator(A_rp, A_ci, A_v, b_diag=bd)
     # the seeded starting block, resident in HBM like the operator; the e2e leg
     # below copies the same block from pinned host memory
@@ -240,7 +245,8 @@ def main():
     h2d = (h_rp.numel() * 4 + h_ci.numel() * 4 + h_v.numel() * 8 +
            (h_b.numel() * 8 if h_b is not None else 0) + X0h.numel() * 8)
     d2h = (lam_h.numel() + X_h.numel() + be_h.numel()) * 8
-    e2e_solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit)
+    e2e_solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit,
+                           dense_eig=args.dense_eig)
     e2e_steps = 0 if args.no_e2e else max(1, args.steps)
     it_e = None
     barrier()

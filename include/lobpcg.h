@@ -71,9 +71,9 @@ typedef struct {
   double tau_ortho;       /* 0: 100 eps; Algorithm 5 orthogonality tolerance */
   double tau_skip;        /* 0: 100 eps; switch to orthogonalisation when cond(R)^-3 < tau_skip (Sec. 5.3) */
   double max_seconds;     /* 0: no limit; host wall-clock limit -> LOBPCG_ERR_TIMEOUT */
-  int32_t dense_eig;      /* eigensolver of the projected matrices: 0 FP32 decomposition
-                             refined to FP64 (Ogita-Aishima steps, cluster Jacobi), 1 FP64
-                             syevd (cuSOLVER) */
+  int32_t dense_eig;      /* eigensolver of the projected matrices: 0 FP64 syevd (cuSOLVER);
+                             1 FP32 syevd refined to FP64 (Ogita-Aishima steps, Newton-Schulz,
+                             cluster Jacobi; FP64 syevd when its residual check fails) */
 } lobpcg_options_t;
 
 /* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
@@ -104,8 +104,8 @@ typedef struct {
   /* BF16 tensor-core work of the emulated contractions: the FP64-equivalent
    * flops times the S(S+1)/2 digit pairs of an S-slice split (0 in FP64 mode) */
   double gram_tensor_flops, update_tensor_flops;
-  /* projected eigenproblems solved, and how many of them fell back to the
-   * FP64 syevd (FP32 stage failed or a cluster wider than 32) */
+  /* projected eigenproblems solved by the refined FP32 eigensolver
+   * (dense_eig 1), and how many of them fell back to the FP64 syevd */
   int64_t eig_calls, eig_fallbacks;
 } lobpcg_stats_t;
 
@@ -249,6 +249,17 @@ int lobpcg_eig_adjoint(lobpcg_t h, int64_t k, const double* lambda, const double
                        int64_t ldx, const double* glam, const double* G, int64_t ldg,
                        int mem_in, double* gA, double* gB, int mem_out, double cg_tol,
                        int32_t cg_maxit, int64_t* cg_iters);
+
+/* Symmetric eigendecomposition of a small dense matrix, the eigensolver of
+ * the projected pencils of Algorithms 2, 4, 6 and 7 (their "eig" step):
+ * A n x n column-major (leading dimension lda, device), symmetric (both
+ * triangles read; it is symmetrised first).  On return A holds the
+ * orthonormal eigenvectors and w (device, n) the eigenvalues ascending.
+ * mode 0: cuSOLVER FP64 syevd; mode 1: FP32 decomposition refined to FP64
+ * (Ogita-Aishima steps, a Newton-Schulz orthonormalisation, Jacobi on
+ * eigenvalue clusters; FP64 syevd when its residual check fails).  n <= 8192.
+ * Allocates its workspace per call and synchronises `stream`. */
+int lobpcg_syev(int64_t n, double* A, int64_t lda, double* w, int mode, void* stream);
 
 /* Philox4x32-10 normals: Y(r, c) = normal number r*m + c of stream `stream_id`
  * under key `seed` (Box-Muller of two 52-bit uniforms), n x m row-major. */

@@ -23,7 +23,7 @@ from ._native import (  # noqa: F401
     lobpcg_create, lobpcg_set_operator, lobpcg_set_precond_diag,
     lobpcg_set_precond_callback, lobpcg_solve, lobpcg_get_stats, lobpcg_last_error,
     lobpcg_destroy, lobpcg_spmm, lobpcg_gram, lobpcg_gram_workspace, lobpcg_gram_noalloc,
-    lobpcg_update, lobpcg_eig_adjoint,
+    lobpcg_update, lobpcg_eig_adjoint, lobpcg_syev,
     lobpcg_residual, lobpcg_philox_normal, load, library_path,
 )
 

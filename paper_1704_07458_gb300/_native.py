@@ -33,7 +33,7 @@ EXPORTED = [
     "lobpcg_set_precond_callback", "lobpcg_solve", "lobpcg_get_stats", "lobpcg_last_error",
     "lobpcg_destroy", "lobpcg_spmm", "lobpcg_gram", "lobpcg_gram_workspace",
     "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
-    "lobpcg_eig_adjoint",
+    "lobpcg_eig_adjoint", "lobpcg_syev",
 ]
 
 
@@ -137,6 +137,7 @@ def load(build_if_missing=False):
                                 P]),
         "lobpcg_residual": (I32, [I64, P, P, P, I64, I64, I64, P, P, P, I64, D, D, P, P]),
         "lobpcg_philox_normal": (I32, [I64, I64, ctypes.c_uint64, ctypes.c_uint32, P, I64, P]),
+        "lobpcg_syev": (I32, [I64, P, I64, P, I32, P]),
         "lobpcg_eig_adjoint": (I32, [P, I64, P, P, I64, P, P, I64, I32, P, P, I32, D, I32,
                                      ctypes.POINTER(I64)]),
     }
@@ -273,3 +274,8 @@ def lobpcg_eig_adjoint(h, k, lam, X, ldx, glam, G, ldg, mem_in, gA, gB, mem_out,
     rc = load().lobpcg_eig_adjoint(h, k, ptr(lam), ptr(X), ldx, ptr(glam), ptr(G), ldg, mem_in,
                                    ptr(gA), ptr(gB), mem_out, cg_tol, cg_maxit, ctypes.byref(it))
     return rc, it.value
+
+
+def lobpcg_syev(n, A, lda, w, mode=0, stream=None):
+    """Eigendecomposition of a small symmetric matrix in place (see lobpcg.h)."""
+    return load().lobpcg_syev(n, ptr(A), lda, ptr(w), mode, stream_ptr(stream))

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) residual_kernel(
     double rn = 0.0, xn = 0.0;
     if (j < m) {
       const double th = theta[j];
+#pragma unroll 4
       for (int64_t r = r0 + ty; r < r1; r += 8) {
         const int64_t o = r * ld + j;
         const double x = X[o];

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kCondThreads) cond_estimate_kernel(int n, cons
 // from X' = X (I + E) with X'^T X' = I and X'^T A X' diagonal to first order
 // (E + E^T = R, E^T D + D E = D - S off the diagonal).
 
-constexpr int kRefineSteps = 2;
+constexpr int kMaxRefineSteps = 6;
 constexpr int kRefBlocks = 64;
 constexpr int kMaxRun = 32;  // cluster blocks up to this size: Jacobi in shared memory
 
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) oa_norms_kernel(int n, const double* __re
 }
 
 // E from S, G and delta (every block reduces the partials itself); block 0
-// stores delta.
+// stores delta and ||A||_F.
 __global__ void __launch_bounds__(256) oa_update_kernel(int n, const double* __restrict__ S,
                                                         const double* __restrict__ G,
                                                         const double* __restrict__ partial,
@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(256) oa_update_kernel(int n, const double* __r
       c += partial[3 * p + 2];
     }
     dl = 2.0 * (sqrt(a) + sqrt(c) * sqrt(b));
-    if (blockIdx.x == 0) *delta_out = dl;
+    if (blockIdx.x == 0) {
+      delta_out[0] = dl;
+      delta_out[1] = sqrt(c);
+    }
   }
   __syncthreads();
   const double delta = dl;
@@ -353,6 +356,24 @@ __global__ void newton_schulz_kernel(int n, double* G) {
   if (e >= (int64_t)n * n) return;
   const int i = (int)(e % n), j = (int)(e / n);
   G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+}
+
+// out = max_i sqrt(sum_{j : runid[j] != runid[i]} S_ij^2) (non-negative
+// doubles order like their bit patterns, so atomicMax on the bits is a max)
+__global__ void offrun_check_kernel(int n, const double* __restrict__ S,
+                                    const int* __restrict__ runid,
+                                    unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int ri = runid[i];
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (runid[j] == ri) continue;
+    const double v = S[i + (int64_t)j * n];
+    acc = fma(v, v, acc);
+  }
+  const double r = sqrt(acc);
+  atomicMax(out, (unsigned long long)__double_as_longlong(isfinite(r) ? r : INFINITY));
 }
 
 __global__ void diag_extract_kernel(int n, const double* __restrict__ S, const double* delta,
@@ -504,11 +525,12 @@ static int syevd_f64(DenseLayer& L, bool vectors, int n, double* A, int lda) {
 }
 
 // Eigenvalues ascending into L.ev, eigenvectors into A (column-major, lda =
-// n), by the FP32 decomposition + FP64 refinement above (eig_mode 0) or
-// cuSOLVER's FP64 syevd (eig_mode 1, and the fallback when the FP32 stage
-// fails, meets a non-finite value or a cluster wider than kMaxRun).
+// n), by cuSOLVER's FP64 syevd (eig_mode 0) or the FP32 decomposition + FP64
+// refinement above (eig_mode 1; FP64 syevd when the FP32 stage fails, meets
+// a non-finite value, a cluster wider than kMaxRun or fails the residual
+// check).
 static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
-  if (L.eig_mode == 1 || n < 2 || lda != n) return syevd_f64(L, vectors, n, A, lda);
+  if (L.eig_mode != 1 || n < 2 || lda != n) return syevd_f64(L, vectors, n, A, lda);
   const int64_t nn = (int64_t)n * n;
   const double one = 1.0, zero = 0.0;
   ++L.eig_calls;
@@ -527,7 +549,11 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
   to_f64_kernel<<<blocks_for(nn), 256, 0, L.st>>>(nn, L.Af, X);
   LAUNCH_OK(L);
   const int nb = (int)std::min<int64_t>(kRefBlocks, ceil_div(nn, 256));
-  for (int step = 0; step < kRefineSteps; ++step) {
+  // refinement steps until delta stops shrinking (it levels off at the width
+  // of the true clusters) or reaches rounding level; delta and ||A||_F come
+  // back to the host after every step
+  double delta = INFINITY, normA = 0.0;
+  for (int step = 0; step < kMaxRefineSteps; ++step) {
     BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, A, lda, X, n, &zero, AX,
                         n));
     BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, X, n, AX, n, &zero, S,
@@ -543,6 +569,18 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
     BLAS_OK(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, X, n, E, n, &one, X1,
                         n));
     std::swap(X, X1);
+    LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                L.st));
+    LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+    const double dnew = L.host[0];
+    normA = L.host[1];
+    if (!std::isfinite(dnew)) {
+      ++L.eig_fallbacks;
+      return syevd_f64(L, vectors, n, A, lda);
+    }
+    const bool level = step > 0 && dnew > 0.25 * delta;
+    delta = dnew;
+    if (level || delta <= 64.0 * n * kEps * normA) break;
   }
   // the steps leave X^T X - I near 1e-13; one Newton-Schulz step restores
   // orthonormality to rounding level
@@ -563,7 +601,6 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
   int info;
   memcpy(&info, L.host + n + 1, sizeof(int));
   const double* d = L.host;
-  const double delta = d[n];
   bool ok = info == 0 && std::isfinite(delta);
   for (int i = 0; ok && i < n; ++i) ok = std::isfinite(d[i]);
   int* perm = L.hint;
@@ -588,8 +625,28 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
     ++L.eig_fallbacks;
     return syevd_f64(L, vectors, n, A, lda);
   }
-  LOB_CUDA_OK(cudaMemcpyAsync(L.dint, L.hint, (size_t)(n + 2 * nruns) * sizeof(int),
-                              cudaMemcpyHostToDevice, L.st));
+  // verification: the coupling of each column to the columns outside its run,
+  // sqrt(sum_j s_ij^2), bounds its final residual ||A z - w z||; above
+  // 8 sqrt(n) eps ||A||_F the refinement has not converged: FP64 syevd instead
+  int* runid = L.hint + n + 2 * nruns;
+  for (int k = 0; k < n; ++k) runid[perm[k]] = k;
+  for (int r = 0; r < nruns; ++r)
+    for (int k = runs[2 * r]; k < runs[2 * r] + runs[2 * r + 1]; ++k) runid[perm[k]] = runs[2 * r];
+  const int nint = 2 * n + 2 * nruns;
+  LOB_CUDA_OK(cudaMemcpyAsync(L.dint, L.hint, (size_t)nint * sizeof(int), cudaMemcpyHostToDevice,
+                              L.st));
+  LOB_CUDA_OK(cudaMemsetAsync(L.scal + 10, 0, sizeof(double), L.st));
+  offrun_check_kernel<<<blocks_for(n), 256, 0, L.st>>>(n, S, L.dint + n + 2 * nruns,
+                                                       (unsigned long long*)(L.scal + 10));
+  LAUNCH_OK(L);
+  double worst = 0.0;
+  LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, L.st));
+  LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  worst = L.host[0];
+  if (!(worst <= 8.0 * std::sqrt((double)n) * kEps * normA)) {
+    ++L.eig_fallbacks;
+    return syevd_f64(L, vectors, n, A, lda);
+  }
   permute_cols_kernel<<<blocks_for(nn), 256, 0, L.st>>>(n, X, S, L.dint, A, lda, L.ev);
   LAUNCH_OK(L);
   if (nruns > 0) {
@@ -629,8 +686,8 @@ int DenseLayer::init(cudaStream_t stream, int64_t n_max) {
   if (cudaMalloc(&Af, (size_t)nmax * nmax * sizeof(float)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&wf, nmax * sizeof(float)) != cudaSuccess) return LOBPCG_ERR_OOM;
   if (cudaMalloc(&part, 3 * kRefBlocks * sizeof(double)) != cudaSuccess) return LOBPCG_ERR_OOM;
-  if (cudaMalloc(&dint, 3 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
-  if (cudaMallocHost(&hint, 3 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(&dint, 4 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMallocHost(&hint, 4 * nmax * sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
   {
     int lws = 0;
     SOL_OK(cusolverDnSsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
@@ -870,3 +927,25 @@ int small_stats(DenseLayer& L, const double* G, int rows, int cols, int ldg, boo
 }
 
 }  // namespace lob
+
+// Kernel-level entry point of the projected eigensolver (see lobpcg.h).
+LOBPCG_EXPORT int lobpcg_syev(int64_t n, double* A, int64_t lda, double* w, int mode,
+                              void* stream) {
+  if (n <= 0 || n > 8192 || lda < n || !A || !w || (mode != 0 && mode != 1))
+    return LOBPCG_ERR_ARG;
+  lob::DenseLayer L;
+  int rc = L.init((cudaStream_t)stream, n);
+  if (!rc) {
+    L.eig_mode = mode;
+    double* M = L.A[0];
+    rc = lob::copy_mat(L, (int)n, (int)n, A, (int)lda, M, (int)n);
+    if (!rc) rc = lob::syevd(L, true, (int)n, M, (int)n);
+    if (!rc) rc = lob::copy_mat(L, (int)n, (int)n, M, (int)n, A, (int)lda);
+    if (!rc && cudaMemcpyAsync(w, L.ev, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st) !=
+                   cudaSuccess)
+      rc = LOBPCG_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(L.st) != cudaSuccess) rc = LOBPCG_ERR_CUDA;
+  }
+  L.release();
+  return rc;
+}

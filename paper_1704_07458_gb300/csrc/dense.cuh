@@ -27,15 +27,16 @@ struct DenseLayer {
   double* scal = nullptr;  // 16 device scalars
   double* host = nullptr;  // pinned host mirror, nmax + 64 doubles
   int64_t launches = 0;
-  // symmetric eigensolver (dense.cu): 0 = FP32 cuSOLVER syevd refined to FP64
-  // (Ogita-Aishima steps + cluster Jacobi), 1 = cuSOLVER FP64 syevd
+  // symmetric eigensolver (dense.cu): 0 = cuSOLVER FP64 syevd, 1 = FP32
+  // cuSOLVER syevd refined to FP64 (Ogita-Aishima steps, Newton-Schulz,
+  // cluster Jacobi, residual check with FP64 fallback)
   int eig_mode = 0;
   int64_t eig_calls = 0, eig_fallbacks = 0;
   double* R[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // refinement blocks
   float *Af = nullptr, *wf = nullptr, *swork = nullptr;
   int lswork = 0;
   double* part = nullptr;  // norm partials of the refinement
-  int* dint = nullptr;     // device permutation + cluster runs (3 nmax)
+  int* dint = nullptr;     // device permutation, cluster runs, run ids (4 nmax)
   int* hint = nullptr;     // pinned host mirror of dint
 
   int init(cudaStream_t stream, int64_t n_max);

@@ -233,7 +233,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
   if ((rc = h->dense.init(h->st, nsmax))) return rc;
-  h->dense.eig_mode = h->opt.dense_eig == 1 ? 1 : 0;
+  h->dense.eig_mode = h->opt.dense_eig == 1 ? 1 : 0;  // 0 FP64 syevd, 1 refined FP32
   h->ws_n = n;
   h->ws_nx = nx;
   h->ws_b = h->b_kind;

@@ -232,15 +232,17 @@ def test_c2_full_size_properties(mode):
 
 @pytest.mark.parametrize("dense_eig", [0, 1])
 def test_projected_eigensolver_forms_agree(dense_eig):
-    """The FP32-decomposition + FP64-refinement eigensolver of the projected
-    pencils (dense_eig 0) and cuSOLVER's FP64 syevd (1) give the same pairs."""
+    """cuSOLVER's FP64 syevd (dense_eig 0) and the FP32-decomposition +
+    FP64-refinement eigensolver of the projected pencils (1) give the same
+    pairs; the refined solver rarely needs its FP64 fallback."""
     p = synth.make_problem("lap3d_64_diagB", N=16, k=16)
     nx = synth.block_width(p.k)
     X0 = synth.normal_block(0, synth.STREAM_X0, p.n, nx)
     lam, X, it, be, rc, st = _gpu(p, X0=X0, mode="f64", dense_eig=dense_eig)
     assert rc == 0
-    if dense_eig == 0:
-        assert st["eig_calls"] >= st["iterations"] and st["eig_fallbacks"] == 0
+    if dense_eig == 1:
+        assert st["eig_calls"] >= st["iterations"]
+        assert st["eig_fallbacks"] <= st["eig_calls"] // 10
     else:
         assert st["eig_calls"] == 0
     _, r = _oracle(p)
