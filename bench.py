@@ -151,6 +151,7 @@ def workload_config(args, p):
                         f"tol={p.tol}", "n": p.n, "nnz": p.A.nnz, "k": p.k, "tol": p.tol,
             "block_width": None, "gemm_mode": args.mode,
             "dense_eig": "fp64_syevd" if getattr(args, "dense_eig", 0) == 0 else "fp32_refined",
+            "ozaki_slices": getattr(args, "slices", 0) or 6,
             "l2": "working set > L2 (15 blocks of n x 72 doubles, 151 MB each); no flush",
             "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "1gpu"}
 
@@ -169,6 +170,8 @@ def main():
                     help="cap the iterations of every solve (0: the solver's default of 2000); "
                          "a capped run is a bounded profile of the same step, not a bench value")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="Ozaki slices of the emulated contractions (0: 6; 3..7)")
     ap.add_argument("--dense-eig", type=int, default=0, choices=[0, 1],
                     help="eigensolver of the projected pencils: 0 FP64 syevd, 1 FP32 refined "
                          "to FP64")
@@ -195,7 +198,7 @@ def main():
     bd = dev(p.b_diag) if p.b_diag is not None else None
 
     solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit,
-                       dense_eig=args.dense_eig)
+                       dense_eig=args.dense_eig, ozaki_slices=args.slices)
     solver.set_operator(A_rp, A_ci, A_v, b_diag=bd)
     # the seeded starting block, resident in HBM like the operator; the e2e leg
     # below copies the same block from pinned host memory
@@ -246,7 +249,7 @@ def main():
            (h_b.numel() * 8 if h_b is not None else 0) + X0h.numel() * 8)
     d2h = (lam_h.numel() + X_h.numel() + be_h.numel()) * 8
     e2e_solver = gb.Solver(stream=stream, gemm_mode=args.mode, maxit=args.maxit,
-                           dense_eig=args.dense_eig)
+                           dense_eig=args.dense_eig, ozaki_slices=args.slices)
     e2e_steps = 0 if args.no_e2e else max(1, args.steps)
     it_e = None
     barrier()
@@ -324,6 +327,7 @@ def main():
         "solver": {"flip_iteration": int(st["flip_iteration"]),
                    "ortho_calls": int(st["ortho_calls"]), "svqb_passes": int(st["svqb_passes"]),
                    "dropped_columns": int(st["dropped_columns"]),
+                   "eig_calls": int(st["eig_calls"]), "eig_fallbacks": int(st["eig_fallbacks"]),
                    "launches_per_solve": int(tot["gpu_launches"]) // max(1, args.steps)},
     }
     line["config"]["block_width"] = int(st["n_x"])
