@@ -37,7 +37,7 @@ WORKLOAD = "lap3d_64_diagB"
 # Iterations the CPU oracle needs to converge on this workload with seed 0
 # (measured by running oracle.lobpcg to convergence on the same inputs); used
 # to extrapolate the bounded oracle samples to a full solve.
-ORACLE_ITERS = {"lap3d_64_diagB": 726}
+ORACLE_ITERS = {"lap3d_64_diagB": 726, "lap2d_32": 101}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores and DMMA), nominal
 
 
@@ -93,6 +93,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(v):
+    """Largest value of v over the ranks (v unchanged on a single process).
+    NCCL reduces a CUDA tensor, gloo a CPU one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -230,10 +243,7 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     ok = (gb.LOBPCG_OK, gb.LOBPCG_ERR_NOT_CONVERGED) if args.maxit else (gb.LOBPCG_OK,)
     assert rc in ok, f"solve failed: {rc}"
     bemax = float(be.max().item())
@@ -264,10 +274,8 @@ def main():
         assert rc_e in ok, rc_e
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps if e2e_steps else None
-    if world > 1 and e2e_s is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    if e2e_s is not None:
+        e2e_s = max_over_ranks(e2e_s)
 
     # ---- roofline of the dominant n-scaled kernel over the timed region
     # FP64 mode: FP64 flops on the CUDA cores ("alu"); emulated modes: the BF16
