@@ -757,7 +757,7 @@ __device__ __forceinline__ void upd_stage_raw(const UpdShared& sh, int64_t n, in
 
 constexpr int kThrAll = kThr + 32;  // 8 compute warps + 1 issuer warp
 constexpr int kIssuerW = kThr;      // issuer thread of the update (warp 8, lane 0)
-constexpr int kOutRows = 64;        // rows of the output staging pass
+constexpr int kOutRows = 128;       // rows of the output staging pass (the whole tile)
 
 template <int S>
 __host__ __device__ inline size_t upd_regionA(int NT) {
@@ -959,8 +959,10 @@ __global__ void __launch_bounds__(kThrAll, 1)
         __syncthreads();
       }
     }
-    // ---- output: Y = acc 2^(E_row + E_col - 14 - kFrac) + beta Y0, in two
-    // passes of 64 rows staged through shared memory (coalesced Y0 and Y)
+    // ---- output: Y = acc 2^(E_row + E_col - 14 - kFrac) + beta Y0, staged
+    // through shared memory (coalesced Y0 and Y) in passes of kOutRows rows;
+    // in a pass every compute warp whose TMEM lane quarter lies in it converts
+    // (with kOutRows = TCM all eight warps convert at once)
     for (int h = 0; h < TCM / kOutRows; ++h) {
       const int64_t rbase = row0 + h * kOutRows;
       if (beta != 0.0 && compute && !failed) {
@@ -971,7 +973,7 @@ __global__ void __launch_bounds__(kThrAll, 1)
         }
       }
       __syncthreads();
-      if (compute && ((warp & 3) >> 1) == h) {
+      if (compute && (32 * (warp & 3)) / kOutRows == h) {
         const int rr = my_r - h * kOutRows;
         const int Er = sh.eA[my_r];
 #pragma unroll
