@@ -9,6 +9,10 @@
   python -m paper_1704_07458_gb300.profiling launches launches.csv
       summarises an ncu launch list (--metrics gpu__time_duration.sum --csv):
       launches, total device time and share per kernel.
+  python -m paper_1704_07458_gb300.profiling forms [--workload lap3d_64_diagB]
+      one timed solve per arithmetic form (FP64, mma.sync emulation, tcgen05
+      emulation with 7, 6, 5 slices): seconds, iterations, backward error and
+      the largest relative eigenvalue difference from the FP64 form.
 """
 import argparse
 import collections
@@ -120,6 +124,40 @@ def time_kernel(which, mode, slices, reps, warmup, n, s, m):
             "gbs": bytes_ / (ms * 1e-3) / 1e9}
 
 
+def compare_forms(workload, forms):
+    """Time one solve of `workload` per arithmetic form and compare its
+    eigenvalues with the FP64 form's (the first form listed must be f64)."""
+    import time
+    import numpy as np
+    import torch
+    import synth
+    from . import Solver
+    p = synth.make_problem(workload, seed=0)
+    nx = synth.block_width(p.k)
+    X0 = torch.from_numpy(synth.normal_block(0, synth.STREAM_X0, p.n, nx)).cuda()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    A = (dev(p.A.rowptr), dev(p.A.col), dev(p.A.val))
+    bd = dev(p.b_diag) if p.b_diag is not None else None
+    ref = None
+    for mode, slices in forms:
+        s = Solver(stream=torch.cuda.current_stream(), gemm_mode=mode, ozaki_slices=slices)
+        s.set_operator(*A, b_diag=bd)
+        s.solve(p.k, p.tol, X0=X0, device=True)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, device=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        lam = lam.cpu().numpy()
+        if ref is None:
+            ref = lam
+        out = {"workload": workload, "mode": mode, "slices": slices or 6, "status": rc,
+               "seconds": dt, "iterations": it, "max_backward_error": float(be.max().item()),
+               "max_rel_lambda_diff_vs_f64": float(np.max(np.abs(lam - ref) / np.abs(ref)))}
+        print(json.dumps(out), flush=True)
+        s.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -134,9 +172,14 @@ def main(argv=None):
     k.add_argument("--m", type=int, default=142)
     l = sub.add_parser("launches")
     l.add_argument("csv")
+    f = sub.add_parser("forms")
+    f.add_argument("--workload", default="lap3d_64_diagB")
     a = ap.parse_args(argv)
     if a.cmd == "launches":
         summarize_launches(a.csv)
+    elif a.cmd == "forms":
+        compare_forms(a.workload, [("f64", 0), ("ozaki", 6), ("ozaki_tc", 7), ("ozaki_tc", 6),
+                                   ("ozaki_tc", 5)])
     else:
         print(json.dumps(time_kernel(a.which, a.mode, a.slices, a.reps, a.warmup, a.n, a.s,
                                      a.m)), flush=True)
