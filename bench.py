@@ -39,6 +39,11 @@ WORKLOAD = "lap3d_64_diagB"
 # to extrapolate the bounded oracle samples to a full solve.
 ORACLE_ITERS = {"lap3d_64_diagB": 726, "lap2d_32": 101}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (CUDA cores and DMMA), nominal
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+# capture of the same kernel build at the workload's shape
+# (profiles/ozaki_update_tc_kernel_n262144_s213_m142.md); None where none is
+# taken.
+NCU_TRAFFIC = {("lap3d_64_diagB", "update", "ozaki_tc", 6): 448.449280e6 + 263.597312e6}
 
 
 def load_peaks():
@@ -311,8 +316,10 @@ def main():
     for k, key in (("gram", "gram_flops"), ("update", "update_flops")):
         t = phases[k][0]
         per_phase[k]["fp64_equivalent_tflops"] = tot[key] / (t * 1e-3) / 1e12 if t > 0 else None
+    traffic = NCU_TRAFFIC.get((args.workload, dom, args.mode, args.slices or 6))
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": None,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": peak_src, "phases": per_phase}
 
     line = {
