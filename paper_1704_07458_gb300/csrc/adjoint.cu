@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(256) shift_dot_kernel(
 }
 
 // CG step with alpha_j = rz_j / pq_j (0 for a finished or broken column):
-// V -= alpha P (V accumulates -u), R -= alpha Q, Z = R / kdiag, partial R^T R.
+// V -= alpha P (V accumulates -u), R -= alpha Q, Z = R kinv (kinv = 1 / diag
+// of the preconditioner), partial R^T R.
 // V may alias P and R may alias Q (the first step runs with alpha = 0 on
 // V = P = 0, R = Q = F to form Z = K^-1 F and |F|^2).
 __global__ void __launch_bounds__(256) cg_step_kernel(
     int64_t n, int k, double* V, const double* P, double* R, const double* Q,
-    double* __restrict__ Z, const double* __restrict__ kdiag, int64_t ld,
+    double* __restrict__ Z, const double* __restrict__ kinv, int64_t ld,
     const double* __restrict__ rz, const double* __restrict__ pq, double* __restrict__ partial) {
   __shared__ double red[8][33];
   const int64_t per = ceil_div(n, (int64_t)gridDim.x);
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) cg_step_kernel(
         V[o] = fma(-a, P[o], V[o]);
         const double rr = fma(-a, Q[o], R[o]);
         R[o] = rr;
-        Z[o] = kdiag ? rr / kdiag[r] : rr;
+        Z[o] = kinv ? rr * kinv[r] : rr;
         s = fma(rr, rr, s);
       }
     }
@@ -254,9 +255,9 @@ int shift_dot(cudaStream_t st, int64_t n, int k, double* Q, const double* P, con
 }
 
 int cg_step(cudaStream_t st, int64_t n, int k, double* V, const double* P, double* R,
-            const double* Q, double* Z, const double* kdiag, int64_t ld, const double* rz,
+            const double* Q, double* Z, const double* kinv, int64_t ld, const double* rz,
             const double* pq, double* rr, void* partial) {
-  cg_step_kernel<<<kRB, 256, 0, st>>>(n, k, V, P, R, Q, Z, kdiag, ld, rz, pq, (double*)partial);
+  cg_step_kernel<<<kRB, 256, 0, st>>>(n, k, V, P, R, Q, Z, kinv, ld, rz, pq, (double*)partial);
   LOB_LAUNCHED();
   return col_finish(st, k, partial, rr);
 }

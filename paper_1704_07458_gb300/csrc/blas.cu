@@ -186,6 +186,22 @@ int update_f64(cudaStream_t st, int64_t n, const SegList& S, const double* C, in
 
 // ------------------------------------------------------- residual and norms
 
+// kinv = 1 / kdiag: the preconditioner is applied as a product, because an
+// FP64 division costs ~10 FP64 instructions on a part whose FP64 rate is 1/64
+// of FP32 (the residual pass was bound by it)
+__global__ void reciprocal_kernel(int64_t n, const double* __restrict__ d,
+                                  double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = 1.0 / d[i];
+}
+
+int reciprocal(cudaStream_t st, int64_t n, const double* d, double* out) {
+  if (n <= 0) return LOBPCG_OK;
+  reciprocal_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, d, out);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
+
 static int row_blocks(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 64), 4 * 152));
 }
@@ -198,7 +214,7 @@ int64_t residual_workspace(int64_t n, int m) {
 __global__ void __launch_bounds__(256) residual_kernel(
     int64_t n, const double* __restrict__ X, const double* __restrict__ AX,
     const double* __restrict__ BX, int64_t ld, int m, int c0, const double* __restrict__ theta,
-    const double* __restrict__ kdiag, double* __restrict__ W, int64_t ldw,
+    const double* __restrict__ kinv, double* __restrict__ W, int64_t ldw,
     double* __restrict__ partial) {
   __shared__ double red[2][8][33];
   const int mm = m - c0;
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(256) residual_kernel(
         const double res = fma(-th, bx, AX[o]);
         rn = fma(res, res, rn);
         xn = fma(x, x, xn);
-        if (W) W[r * ldw + (j - c0)] = kdiag ? res / kdiag[r] : res;
+        if (W) W[r * ldw + (j - c0)] = kinv ? res * kinv[r] : res;
       }
     }
     red[0][ty][tx] = rn;
@@ -251,12 +267,12 @@ __global__ void residual_finish_kernel(const double* __restrict__ partial, int b
 }
 
 int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, const double* BX,
-             int64_t ld, int m, int c0, const double* theta, const double* kdiag, double* W,
+             int64_t ld, int m, int c0, const double* theta, const double* kinv, double* W,
              int64_t ldw, double normA, double normB, double* be, void* partial) {
   const int mm = m - c0;
   if (mm <= 0) return LOBPCG_OK;
   const int blocks = row_blocks(n);
-  residual_kernel<<<blocks, 256, 0, st>>>(n, X, AX, BX, ld, m, c0, theta, kdiag, W, ldw,
+  residual_kernel<<<blocks, 256, 0, st>>>(n, X, AX, BX, ld, m, c0, theta, kinv, W, ldw,
                                           (double*)partial);
   LOB_LAUNCHED();
   residual_finish_kernel<<<(unsigned)ceil_div(mm, 128), 128, 0, st>>>(
@@ -560,11 +576,14 @@ LOBPCG_EXPORT int lobpcg_residual(int64_t n, const double* X, const double* AX,
   if (!X || !AX || ld < m || !theta || !be || (W && ldw < m - c0)) return LOBPCG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   void* part = nullptr;
-  if (cudaMallocAsync(&part, (size_t)lob::residual_workspace(n, (int)(m - c0)), st) !=
-      cudaSuccess)
+  const size_t pb = (size_t)lob::residual_workspace(n, (int)(m - c0));
+  if (cudaMallocAsync(&part, pb + (kdiag ? (size_t)n * sizeof(double) : 0), st) != cudaSuccess)
     return LOBPCG_ERR_OOM;
-  int rc = lob::residual(st, n, X, AX, BX, ld, (int)m, (int)c0, theta, kdiag, W, ldw, normA,
-                         normB, be, part);
+  double* kinv = kdiag ? (double*)((char*)part + pb) : nullptr;
+  int rc = kdiag ? lob::reciprocal(st, n, kdiag, kinv) : LOBPCG_OK;
+  if (!rc)
+    rc = lob::residual(st, n, X, AX, BX, ld, (int)m, (int)c0, theta, kinv, W, ldw, normA, normB,
+                       be, part);
   cudaFreeAsync(part, st);
   return rc;
 }

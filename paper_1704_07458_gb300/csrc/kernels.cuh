@@ -54,12 +54,15 @@ int update_ozaki(cudaStream_t st, int64_t n, const SegList& S, const double* C, 
                  int slices, void* work, int64_t work_bytes, const int* colexp = nullptr);
 int64_t update_ozaki_workspace(int64_t n, int s, int m, int slices);
 
-// Residual / preconditioner / Eq. (9) norms for columns c0..m-1.
+// Residual / preconditioner / Eq. (9) norms for columns c0..m-1; the
+// preconditioner enters as its reciprocal diagonal kinv (nullptr: K = I).
 // partial: device scratch of residual_workspace(n, m) bytes.
 int64_t residual_workspace(int64_t n, int m);
 int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, const double* BX,
-             int64_t ld, int m, int c0, const double* theta, const double* kdiag, double* W,
+             int64_t ld, int m, int c0, const double* theta, const double* kinv, double* W,
              int64_t ldw, double normA, double normB, double* be, void* partial);
+// out = 1 / d (n values)
+int reciprocal(cudaStream_t st, int64_t n, const double* d, double* out);
 
 // Column sums of squares of an n x m block: out[j] = sum_i Y(i, j)^2 (fixed order).
 int64_t colsumsq_workspace(int64_t n, int m);
@@ -99,9 +102,9 @@ int adj_coeff(cudaStream_t st, int k, const double* M, int64_t ldm, const double
 // Q -= (B P) diag(lam) (BP given, or diagonal b, or B = I); out_j = P_j^T Q_j.
 int shift_dot(cudaStream_t st, int64_t n, int k, double* Q, const double* P, const double* BP,
               const double* b, int64_t ld, const double* lam, double* out, void* partial);
-// alpha = rz/pq: V -= alpha P, R -= alpha Q, Z = R / kdiag (kdiag null: Z = R), rr = |R_j|^2.
+// alpha = rz/pq: V -= alpha P, R -= alpha Q, Z = R kinv (kinv null: Z = R), rr = |R_j|^2.
 int cg_step(cudaStream_t st, int64_t n, int k, double* V, const double* P, double* R,
-            const double* Q, double* Z, const double* kdiag, int64_t ld, const double* rz,
+            const double* Q, double* Z, const double* kinv, int64_t ld, const double* rz,
             const double* pq, double* rr, void* partial);
 int coldot(cudaStream_t st, int64_t n, int k, const double* X, const double* Y, int64_t ld,
            double* out, void* partial);

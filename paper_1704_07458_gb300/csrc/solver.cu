@@ -123,6 +123,7 @@ struct lobpcg_ctx {
   double *X, *P, *AX, *AP, *AW, *BX, *BP, *BW, *Xn, *Pn, *AXn, *APn, *BXn, *BPn, *Om;
   double* wbuf[4];
   double *theta, *be, *colA, *colB, *Gw, *Gs, *SAS, *SBS, *Cm, *PAP, *PAPn;
+  double* kinv = nullptr;  // 1 / diag(K) for the current solve (n)
   int *cexp, *zexp;  // column balance exponents of S, and all zeros
   void* gwork = nullptr;
   int64_t gwork_bytes = 0;
@@ -208,6 +209,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   for (double** b : vecs)
     if ((rc = dalloc(h, (void**)b, (size_t)std::max<int64_t>(nsmax, s) * 2 * sizeof(double))))
       return rc;
+  if ((rc = dalloc(h, (void**)&h->kinv, (size_t)n * sizeof(double)))) return rc;
   if ((rc = dalloc(h, (void**)&h->cexp, (size_t)nsmax * sizeof(int)))) return rc;
   if ((rc = dalloc(h, (void**)&h->zexp, (size_t)nsmax * sizeof(int)))) return rc;
   LOB_CUDA_OK(cudaMemsetAsync(h->zexp, 0, (size_t)nsmax * sizeof(int), h->st));
@@ -461,6 +463,10 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   if (h->opt.implicit == 1) implicit = false;
   if (h->opt.implicit == 2) implicit = true;
   const double* kd = (h->k_kind == 0) ? h->adiag : (h->k_kind == 1 ? h->kdiag : nullptr);
+  if (kd) {
+    if ((rc = reciprocal(h->st, n, kd, h->kinv))) return rc;
+    kd = h->kinv;  // the residual pass applies K^-1 as a product
+  }
   std::vector<double> be_h(std::max<int64_t>(nx, s) + 8), th_h(nx);
 
   // ---- Sec. 4.3: Gaussian-sketch norm estimates ||M||^(Omega) = ||M Omega^T||_F / ||Omega||_F
@@ -862,6 +868,10 @@ int adjoint_impl(lobpcg_ctx* h, int64_t k64, const double* lambda, const double*
                      "two wanted eigenvalues are closer than 1e-10 max(|lambda|, ||A||)");
     }
     const double* kd = (h->k_kind == 0) ? h->adiag : (h->k_kind == 1 ? h->kdiag : nullptr);
+    if (kd) {  // cg_step applies K^-1 as a product with the reciprocal
+      if ((rc = reciprocal(st, n, kd, h->kinv))) return rc;
+      kd = h->kinv;
+    }
     // project Z onto the B-orthogonal complement of X: Z -= X (BX^T Z)
     auto project = [&]() -> int {
       int r;

@@ -91,21 +91,43 @@ def time_kernel(which, mode, slices, reps, warmup, n, s, m):
         tensor = 2.0 * n * s * m * pairs(slices) if mode != "f64" else 0.0
         bytes_ = 8.0 * n * (s + m)
     elif which == "spmm":
+        # the solver's shape: A W with the diagonal-B product fused, blocks
+        # with the leading dimension rounded up to 8 doubles
         import synth
         A = synth.laplacian_3d_dirichlet(64)
         n = A.n
+        ld = (m + 7) // 8 * 8
         rp = torch.from_numpy(A.rowptr).cuda()
         ci = torch.from_numpy(A.col).cuda()
         va = torch.from_numpy(A.val).cuda()
-        X = torch.randn(n, m, generator=g, **dev)
-        Y = torch.empty(n, m, **dev)
+        b = torch.rand(n, generator=g, **dev) + 1.0
+        X = torch.randn(n, ld, generator=g, **dev)
+        Y = torch.empty(n, ld, **dev)
+        BY = torch.empty(n, ld, **dev)
 
         def run():
-            rc = nat.lobpcg_spmm(n, rp, ci, va, X, m, m, Y, m, None, None, 0, st)
+            rc = nat.lobpcg_spmm(n, rp, ci, va, X, ld, m, Y, ld, b, BY, ld, st)
             assert rc == 0, rc
         flops = 2.0 * A.nnz * m
         tensor = 0.0
-        bytes_ = 12.0 * A.nnz + 4.0 * (n + 1) + 16.0 * n * m
+        bytes_ = 12.0 * A.nnz + 4.0 * (n + 1) + 16.0 * n * m + 8.0 * n + 16.0 * n * m
+    elif which == "residual":
+        # R = AX - BX diag(theta), W = R / kdiag, Eq. (9) norms; diagonal B
+        ld = (m + 7) // 8 * 8
+        X = torch.randn(n, ld, generator=g, **dev)
+        AX = torch.randn(n, ld, generator=g, **dev)
+        BX = torch.randn(n, ld, generator=g, **dev)
+        W = torch.empty(n, ld, **dev)
+        th = torch.rand(m, generator=g, **dev)
+        kd = torch.rand(n, generator=g, **dev) + 1.0
+        be = torch.empty(m, **dev)
+
+        def run():
+            rc = nat.lobpcg_residual(n, X, AX, BX, ld, m, 0, th, kd, W, ld, 12.0, 2.0, be, st)
+            assert rc == 0, rc
+        flops = 0.0
+        tensor = 0.0
+        bytes_ = 8.0 * n * m * 4 + 8.0 * n
     else:
         raise ValueError(which)
     for _ in range(warmup):
@@ -162,7 +184,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     k = sub.add_parser("kernel")
-    k.add_argument("which", choices=["update", "gram", "spmm"])
+    k.add_argument("which", choices=["update", "gram", "spmm", "residual"])
     k.add_argument("--mode", default="ozaki_tc", choices=["f64", "ozaki", "ozaki_tc"])
     k.add_argument("--slices", type=int, default=6)
     k.add_argument("--reps", type=int, default=5)
