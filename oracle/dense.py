@@ -1,7 +1,7 @@
 """Dense FP64 building blocks of the oracle (test infrastructure only).
 
 This module is part of the CPU oracle that the tests, the smoke check and the
-benchmark's CPU baseline use to judge the CUDA library.  The product path never
+benchmark's CPU baseline use to check the CUDA library.  The product path never
 imports it.
 
   jacobi_eigh      cyclic Jacobi eigensolver (Golub & Van Loan, Matrix
