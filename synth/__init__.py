@@ -13,7 +13,8 @@ from .philox import (philox4x32_10, uniform52, normal_flat, normal_block, unifor
                      STREAM_OMEGA, STREAM_GRAD)
 from .problems import (CSR, Problem, laplacian_1d, laplacian_2d_dirichlet,
                        laplacian_3d_dirichlet, diffusion_3d_lognormal,
-                       hamiltonian_3d_periodic, tridiag, add_diagonal,
+                       hamiltonian_3d_periodic, tridiag, add_diagonal, mass_matrix_2d,
+                       closed_form_mass_pencil,
                        block_width, make_problem, WORKLOADS)
 
 __all__ = [
@@ -22,6 +23,7 @@ __all__ = [
     "STREAM_OMEGA", "STREAM_GRAD",
     "CSR", "Problem", "laplacian_1d", "laplacian_2d_dirichlet",
     "laplacian_3d_dirichlet", "diffusion_3d_lognormal",
-    "hamiltonian_3d_periodic", "tridiag", "add_diagonal", "block_width",
+    "hamiltonian_3d_periodic", "tridiag", "add_diagonal", "mass_matrix_2d",
+    "closed_form_mass_pencil", "block_width",
     "make_problem", "WORKLOADS",
 ]

@@ -175,6 +175,26 @@ def hamiltonian_3d_periodic(nx, potential):
                          lambda s, t, a: np.full(len(s), -0.5))
 
 
+def mass_matrix_2d(nx, c, ny=None):
+    """B = I + c * (adjacency of the 5-point grid), the pattern of the 2D
+    Dirichlet Laplacian: SPD for |c| < 1/4, and it shares the Laplacian's
+    sine eigenvectors (both are polynomials in the grid adjacency)."""
+    L = laplacian_2d_dirichlet(nx, ny)
+    rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+    val = np.where(rows == L.col, 1.0, -c * L.val)
+    return CSR(L.n, L.rowptr, L.col, val)
+
+
+def closed_form_mass_pencil(nx, c, count, ny=None):
+    """Lowest eigenvalues of (Laplacian, I + c Adj) on the nx x ny Dirichlet
+    grid: (4 - mu) / (1 + c mu), mu = 2 cos(pi i/(nx+1)) + 2 cos(pi j/(ny+1))."""
+    ny = ny or nx
+    i = np.arange(1, nx + 1)[:, None]
+    j = np.arange(1, ny + 1)[None, :]
+    mu = 2 * np.cos(np.pi * i / (nx + 1)) + 2 * np.cos(np.pi * j / (ny + 1))
+    return np.sort(((4 - mu) / (1 + c * mu)).ravel())[:count]
+
+
 def add_diagonal(a, d):
     """A + diag(d) for a CSR A whose diagonal entries are all stored."""
     rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))

@@ -205,3 +205,34 @@ def test_adjoint_c5_full_size_properties():
     want = np.einsum("ei,ei->e", Xh[rows], Xh[p.A.col])
     assert np.abs(gA1.cpu().numpy() - want).max() <= 1e-14 * k
     s.close()
+
+
+def test_adjoint_csr_metric():
+    """Sparse B = I + 0.2 * grid adjacency with A = Lap + diag(V) on 8 x 8:
+    gA on A's pattern and gB on B's pattern against the oracle."""
+    torch_cuda()
+    k = 6
+    p, G, _ = _instance(8, k)
+    Bm = synth.mass_matrix_2d(8, 0.2)
+    glam = np.linspace(1.0, 2.0, k)
+    A = p.A.to_dense()
+    lam_o, X_o, GA, GB = og.grad_full(A, Bm.to_dense(), k, glam, G)
+    from oracle import dense
+    lam_all, _ = dense.pencil_eigh(A, Bm.to_dense(), use_jacobi=False)
+    _, b2 = _bounds(lam_all, k, 1e-11, np.abs(lam_all).max() * 2.0, G)
+    s = gb.Solver(gemm_mode="f64")
+    s.set_operator(p.A.rowptr, p.A.col, p.A.val,
+                   b_csr=(np.ascontiguousarray(Bm.rowptr, dtype=np.int32),
+                          np.ascontiguousarray(Bm.col, dtype=np.int32),
+                          np.ascontiguousarray(Bm.val, dtype=np.float64)))
+    nx = synth.block_width(k, p.n)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, nx)
+    lam, X, it, be, rc = s.solve(k, 1e-11, X0=X0)
+    assert rc == gb.LOBPCG_OK
+    np.testing.assert_allclose(lam, lam_o, rtol=1e-9)
+    gA, gB, its, rc = s.adjoint(k, lam, X, glam, G, cg_tol=CG_TOL)
+    assert rc == gb.LOBPCG_OK and gB is not None and len(gB) == len(Bm.val)
+    ea = np.abs(gA - og.on_pattern(GA, p.A.rowptr, p.A.col)).max()
+    eb = np.abs(gB - og.on_pattern(GB, Bm.rowptr, Bm.col)).max()
+    assert ea <= b2 and eb <= b2 * np.abs(lam_all[:k]).max(), (ea, eb, b2)
+    s.close()

@@ -248,3 +248,36 @@ def test_projected_eigensolver_forms_agree(dense_eig):
     _, r = _oracle(p)
     np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
     _check_pairs(p, lam, X, be, r.normA, r.normB)
+
+
+@pytest.mark.parametrize("mode", ["f64", "ozaki_tc"])
+def test_csr_metric_closed_form(mode):
+    """Sparse B = I + 0.2 * grid adjacency with the 2D Laplacian on 32 x 32:
+    closed-form eigenvalues, the oracle, B-orthonormality and Eq. (9) with
+    explicit products (implicit updates are off for a sparse B)."""
+    torch_cuda()
+    N, c, k = 32, 0.2, 8
+    A = synth.laplacian_2d_dirichlet(N)
+    B = synth.mass_matrix_2d(N, c)
+    nx = synth.block_width(k)
+    X0 = synth.normal_block(0, synth.STREAM_X0, A.n, nx)
+    s = gb.Solver(gemm_mode=mode)
+    s.set_operator(A.rowptr, A.col, A.val,
+                   b_csr=(np.ascontiguousarray(B.rowptr, dtype=np.int32),
+                          np.ascontiguousarray(B.col, dtype=np.int32),
+                          np.ascontiguousarray(B.val, dtype=np.float64)))
+    lam, X, it, be, rc = s.solve(k, 1e-8, X0=X0)
+    st = s.stats()
+    s.close()
+    assert rc == 0
+    np.testing.assert_allclose(lam, synth.closed_form_mass_pencil(N, c, k), rtol=1e-9)
+    pen = L.Pencil(A.n, (A.rowptr, A.col, A.val), (B.rowptr, B.col, B.val), A.diagonal())
+    Om = synth.normal_block(0, synth.STREAM_OMEGA, A.n, 16).T
+    r = L.lobpcg(pen, X0, k, 1e-8, Om)
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    Bs = sp.csr_matrix((B.val, B.col, B.rowptr), shape=(A.n, A.n))
+    As = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    np.testing.assert_allclose(X.T @ (Bs @ X), np.eye(k), atol=1e-12)
+    R = As @ X - (Bs @ X) * lam[None, :]
+    ref = L.backward_error(R, X, lam, st["norm_a"], st["norm_b"])
+    assert np.all(ref <= 1e-8 * (1 + 1e-6))

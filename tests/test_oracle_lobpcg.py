@@ -353,3 +353,26 @@ def test_breakdown_and_not_converged():
     X0 = synth.normal_block(0, 1, A.n, 4)
     r = L.lobpcg(pen, X0, 2, 1e-8, Om, L.Options(maxit=3))
     assert r.status == L.NOT_CONVERGED and r.iters == 3
+
+
+def test_csr_metric_closed_form_and_brute_force():
+    """Sparse B (I + c * grid adjacency): the pencil with the 2D Laplacian has
+    the closed form (4 - mu) / (1 + c mu); the closed form itself is checked
+    against the dense pencil solver on a small grid."""
+    N, c = 6, 0.2
+    A = synth.laplacian_2d_dirichlet(N)
+    B = synth.mass_matrix_2d(N, c)
+    w, _ = dense.pencil_eigh(A.to_dense(), B.to_dense(), use_jacobi=True)
+    np.testing.assert_allclose(w, synth.closed_form_mass_pencil(N, c, N * N), rtol=1e-12)
+    N, k = 20, 6
+    A = synth.laplacian_2d_dirichlet(N)
+    B = synth.mass_matrix_2d(N, c)
+    pen = L.Pencil(A.n, (A.rowptr, A.col, A.val), (B.rowptr, B.col, B.val), A.diagonal())
+    nx = synth.block_width(k)
+    X0 = synth.normal_block(0, synth.STREAM_X0, A.n, nx)
+    Om = synth.normal_block(0, synth.STREAM_OMEGA, A.n, 16).T
+    r = L.lobpcg(pen, X0, k, 1e-10, Om)
+    assert r.status == L.OK
+    np.testing.assert_allclose(r.lam, synth.closed_form_mass_pencil(N, c, k), rtol=1e-9)
+    Bd = B.to_dense()
+    np.testing.assert_allclose(r.X.T @ Bd @ r.X, np.eye(k), atol=1e-12)
