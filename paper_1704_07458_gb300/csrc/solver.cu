@@ -298,8 +298,10 @@ int apply_AB(lobpcg_ctx* h, const double* X, int m, double* AY, double* BY) {
   h->stats.spmm_calls++;
   h->stats.spmm_bytes += h->A_nnz * 12.0 + 4.0 * (n + 1) + 16.0 * n * m +
                          ((BY && h->b_kind == 1) ? 8.0 * n + 16.0 * n * m : 0.0);
+  // the diagonal-B product rides along with A X; a sparse B gets its own pass
+  const bool fused = BY && h->b_kind == 1;
   int rc = spmm(h->st, h->n, h->A_rp, h->A_ci, h->A_v, X, h->ld, m, AY, h->ld,
-                (BY && h->b_kind == 1) ? h->b_diag : nullptr, BY, h->ld);
+                fused ? h->b_diag : nullptr, fused ? BY : nullptr, h->ld);
   if (rc || !BY) return rc;
   if (h->b_kind == 2)
     rc = spmm(h->st, h->n, h->B_rp, h->B_ci, h->B_v, X, h->ld, m, BY, h->ld, nullptr, nullptr, 0);

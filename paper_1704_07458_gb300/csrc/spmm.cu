@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) spmm_csr_kernel(
       const int c = c0 + lane + t * TPR;
       if (c < m) {
         Y[row * ldy + c] = acc[t];
-        if (BY) BY[row * ldby + c] = b[row] * X[row * ldx + c];
+        if (b && BY) BY[row * ldby + c] = b[row] * X[row * ldx + c];
       }
     }
   }
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) spmm_csr_wide_kernel(
       }
     }
   }
-  const double br = BY ? b[row] : 0.0;
+  const bool fuse = b != nullptr && BY != nullptr;
+  const double br = fuse ? b[row] : 0.0;
 #pragma unroll
   for (int t = 0; t < CP; ++t) {
     const int q = lane + 32 * t;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256) spmm_csr_wide_kernel(
       const int c = 2 * q;
       Y[row * ldy + c] = acc[t].x;
       if (c + 1 < m) Y[row * ldy + c + 1] = acc[t].y;
-      if (BY) {
+      if (fuse) {
         const double2 x = __ldg(reinterpret_cast<const double2*>(X + row * ldx) + q);
         BY[row * ldby + c] = br * x.x;
         if (c + 1 < m) BY[row * ldby + c + 1] = br * x.y;
@@ -158,6 +159,7 @@ LOBPCG_EXPORT int lobpcg_spmm(int64_t n, const int32_t* rowptr, const int32_t* c
   if (n > 0 && m > 0 && (!rowptr || !col || !val || !X || !Y || ldx < m || ldy < m))
     return LOBPCG_ERR_ARG;
   if (b && (!BY || ldby < m)) return LOBPCG_ERR_ARG;
+  if (BY && !b) return LOBPCG_ERR_ARG;
   return lob::spmm((cudaStream_t)stream, n, rowptr, col, val, X, ldx, (int)m, Y, ldy, b, BY,
                    ldby);
 }
