@@ -200,8 +200,10 @@ def test_adjoint_c5_full_size_properties():
     assert rc in (gb.LOBPCG_OK, gb.LOBPCG_ERR_NOT_CONVERGED) and its > 0
     vals = dev(p.A.val)
     euler = float((gA * vals).sum())
-    # X^T X = I to ~1e-12 leaves x_i^T w_i^in at ~1e-12 |G| / gap
-    assert abs(euler - float(lam.sum())) <= 1e-7 * float(lam.abs().sum()) + 1e-12 * float(
+    # for computed pairs the identity carries sum_i w_i^T r_i (r_i the
+    # residual, |r_i| ~ 1e-8 ||A||) and x_i^T w_i^in (X^T X = I to ~1e-12);
+    # measured 1.3e-7 relative: a wrong coefficient anywhere gives O(1)
+    assert abs(euler - float(lam.sum())) <= 1e-6 * float(lam.abs().sum()) + 1e-12 * float(
         (gA.abs() * vals.abs()).sum())
     gA1, _, its1, rc1 = s.adjoint(k, lam, X, glam, None)
     assert rc1 == gb.LOBPCG_OK and its1 == 0
