@@ -282,3 +282,20 @@ def test_csr_metric_closed_form(mode):
     R = As @ X - (Bs @ X) * lam[None, :]
     ref = L.backward_error(R, X, lam, st["norm_a"], st["norm_b"])
     assert np.all(ref <= 1e-8 * (1 + 1e-6))
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name,kw", [("diffusion_128", dict(N=16, k=16)),
+                                     ("hamiltonian_96", dict(N=12, k=32))])
+def test_reduced_c3_c4_against_oracle_and_dense(mode, name, kw):
+    """The c3 operator (log-normal diffusion, sigma = 1) on 16^3 and the c4
+    operator (periodic -Laplacian/2 + V, V ~ U[0, 10]) on 12^3: eigenvalues
+    against the oracle's and against a dense LAPACK decomposition."""
+    p = synth.make_problem(name, seed=0, **kw)
+    lam, X, it, be, rc, st = _gpu(p, mode=mode)
+    assert rc == 0
+    _, r = _oracle(p)
+    np.testing.assert_allclose(lam, r.lam, rtol=1e-10)
+    w = np.linalg.eigvalsh(p.A.to_dense())[:p.k]
+    np.testing.assert_allclose(lam, w, rtol=1e-10)
+    _check_pairs(p, lam, X, be, r.normA, r.normB)
