@@ -123,7 +123,7 @@ int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, void* stream);
 /* Set the pencil.  A: CSR (n, A_nnz).  B: either CSR (B_rowptr != NULL), or a
  * diagonal (B_diag != NULL, n values), or the identity (both NULL).  `mem`
  * says whether the arrays are host or device pointers; they are copied.
- * Resets the preconditioner to Jacobi K = diag(A) (Algorithm 1, line 7 / Eq. 2).
+ * Resets the preconditioner to Jacobi K = diag(A) (Algorithm 1, Eq. 2).
  * Errors: LOBPCG_ERR_ARG for n <= 0, a zero diagonal entry of A (Jacobi), or
  * nnz >= 2^31. */
 int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
@@ -208,7 +208,7 @@ int lobpcg_update(int64_t n, const double* S, int64_t lds, int64_t s, const doub
                   int64_t ldc, int64_t m, double alpha, double beta, const double* Y0,
                   int64_t ldy0, double* Y, int64_t ldy, int mode, int slices, void* stream);
 
-/* Residual, preconditioner and norms (Algorithm 8, lines 8-9 and 17-18):
+/* Residual, preconditioner and norms (the residual, W and convergence steps of Algorithm 8):
  * for columns j = c0 .. m-1: r_j = AX_j - theta_j BX_j (BX == NULL: B = I),
  * W(:, j - c0) = r_j / kdiag (kdiag == NULL: K = I), and
  * be_j = ||r_j|| / ((normA + |theta_j| normB) ||x_j||)  (Eq. 9) written to

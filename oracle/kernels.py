@@ -36,5 +36,5 @@ def update(S, C):
 
 
 def residual(AX, BX, theta):
-    """R = AX - BX Theta (Algorithm 8, line 17)."""
+    """R = AX - BX Theta (the residual of Algorithm 8)."""
     return AX - BX * theta[None, :]

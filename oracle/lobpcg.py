@@ -20,7 +20,7 @@ implementation of LOBPCG", 2018):
 Readings where the paper is silent or inconsistent (each is a documented
 choice, identical in the CUDA library):
   * block width n_x = k + max(ceil(k/10), 2)  (Sec. 6: "padded by about 10%").
-  * K^-1 is applied to R in both branches of Algorithm 8 (its lines 8-9 write
+  * K^-1 is applied to R in both branches of Algorithm 8 (its W step writes
     R, Algorithm 1 and Eq. (2) apply K^-1).
   * tau_replace = tau_drop = n_u * eps, tau_ortho = 100 eps, tau_skip = 100 eps,
     eps = 2^-52; all norms in the orthogonality tests are Frobenius norms.
@@ -351,7 +351,7 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
     implicit = {"auto": pencil.implicit_allowed(), "always": True,
                 "never": False}[opts.implicit]
 
-    # Algorithm 8, lines 3-6: initial Rayleigh-Ritz on X0 (Algorithm 2)
+    # Algorithm 8, initial step: Rayleigh-Ritz on X0 (Algorithm 2)
     AX0, BX0 = pencil.A_mul(X0), pencil.B_mul(X0)
     try:
         C, theta = rayleigh_ritz(X0.T @ AX0, X0.T @ BX0)
@@ -404,13 +404,13 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
             rr = rayleigh_ritz_modified(SAS, SBS, nx, nc, use_ortho, opts.tau_skip)
             stats["condR"].append(rr.condR)
             if rr.flip:
-                # Algorithm 8, lines 12-15
+                # Algorithm 8: switch to orthogonalisation and project again
                 use_ortho = True
                 stats["flip_iter"] = it
                 W, BW, AW = make_w(True)
                 SAS, SBS = project(W, AW, BW)
                 rr = rayleigh_ritz_modified(SAS, SBS, nx, nc, True, opts.tau_skip)
-            # Algorithm 8, line 16 and Sec. 5.2
+            # Algorithm 8 update and Sec. 5.2
             S = np.hstack([X, P, W])
             Xn, Pn = S @ rr.Cx, S @ rr.Cp
             if implicit and not refresh_next and it % opts.refresh_every != 0:
@@ -425,7 +425,7 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
                 BXn, BPn = pencil.B_mul(Xn), pencil.B_mul(Pn)
             X, P, AX, AP, BX, BP = Xn, Pn, AXn, APn, BXn, BPn
             theta, PAP = rr.theta, rr.PAP
-            # Algorithm 8, lines 17-18
+            # Algorithm 8: residual and convergence test
             R = AX - BX * theta[None, :]
             be = backward_error(R, X, theta, normA, normB)
             nc_new = max(nc, min(leading_converged(be, tol), nx))

@@ -488,7 +488,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.norm_a = normA;
   h->stats.norm_b = normB;
 
-  // ---- Algorithm 8, lines 3-6: X = X0 C with [C, Theta] = RayleighRitz(X0)
+  // ---- Algorithm 8, initial step: X = X0 C with [C, Theta] = RayleighRitz(X0)
   if (X0) {
     LOB_CUDA_OK(cudaMemcpy2DAsync(h->X, ld * sizeof(double), X0, ldx0 * sizeof(double),
                                   nx * sizeof(double), n,
@@ -612,7 +612,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
           return rc;
       }
       if (flip) {
-        // Algorithm 8, lines 12-15
+        // Algorithm 8: switch to orthogonalisation, redo basis selection and projection
         use_ortho = true;
         h->stats.flip_iteration = it;
         if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
@@ -623,7 +623,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
                               &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
           return rc;
       }
-      // Algorithm 8, line 16 and Sec. 5.2: [X, P] = S [C_x, C_p] (+ implicit products)
+      // Algorithm 8 update and Sec. 5.2: [X, P] = S [C_x, C_p] (+ implicit products)
       const int mo = (int)nx + npn;
       const bool refresh = refresh_next || (it % refresh_every == 0);
       const int* bal = h->zexp;
@@ -671,7 +671,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       std::swap(h->BP, h->BPn);
       std::swap(h->PAP, h->PAPn);
       np = npn;
-      // Algorithm 8, lines 17-18
+      // Algorithm 8: residual, preconditioned W and the convergence test
       Wbase = (Wbase == h->wbuf[0]) ? h->wbuf[1] : h->wbuf[0];
       if ((rc = residual_step(nc, true))) return rc;
       if ((rc = to_host(h, be_h.data(), h->be, nx - nc))) return rc;
