@@ -343,6 +343,7 @@ def main():
                    "ortho_calls": int(st["ortho_calls"]), "svqb_passes": int(st["svqb_passes"]),
                    "dropped_columns": int(st["dropped_columns"]),
                    "eig_calls": int(st["eig_calls"]), "eig_fallbacks": int(st["eig_fallbacks"]),
+                   "slice_escalation_iteration": int(st["slice_escalation_iteration"]),
                    "launches_per_solve": int(tot["gpu_launches"]) // max(1, args.steps)},
     }
     line["config"]["block_width"] = int(st["n_x"])

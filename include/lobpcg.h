@@ -66,7 +66,8 @@ typedef struct {
                              (Sec. 4.3).  Omega^T is the n x s block whose element (r, c) is
                              normal number r*s + c of Philox stream 5 under the solve's seed */
   int32_t gemm_mode;      /* lobpcg_gemm_mode; 0 selects LOBPCG_GEMM_F64 */
-  int32_t ozaki_slices;   /* 0: 6; BF16 slices per operand for LOBPCG_GEMM_OZAKI (3..7) */
+  int32_t ozaki_slices;   /* 0: 6; BF16 slices per operand for the emulated modes (3..7); a
+                             solve that stalls at the contraction accuracy continues with 7 */
   int32_t certify;        /* 0: on; 1: off.  Explicit-product re-check of Eq. (9) at exit */
   double tau_ortho;       /* 0: 100 eps; Algorithm 5 orthogonality tolerance */
   double tau_skip;        /* 0: 100 eps; switch to orthogonalisation when cond(R)^-3 < tau_skip (Sec. 5.3) */
@@ -107,6 +108,10 @@ typedef struct {
   /* projected eigenproblems solved by the refined FP32 eigensolver
    * (dense_eig 1), and how many of them fell back to the FP64 syevd */
   int64_t eig_calls, eig_fallbacks;
+  /* emulated forms: iteration at which a stall (no column converging and the
+   * leading backward error flat over 400 iterations) raised the contractions
+   * to 7 slices for the rest of the solve; -1 never */
+  int64_t slice_escalation_iteration;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.

@@ -85,6 +85,7 @@ class lobpcg_stats_t(ctypes.Structure):
         ("update_tensor_flops", ctypes.c_double),
         ("eig_calls", ctypes.c_int64),
         ("eig_fallbacks", ctypes.c_int64),
+        ("slice_escalation_iteration", ctypes.c_int64),
     ]
 
     def as_dict(self):

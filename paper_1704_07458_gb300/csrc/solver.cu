@@ -124,6 +124,7 @@ struct lobpcg_ctx {
   double* wbuf[4];
   double *theta, *be, *colA, *colB, *Gw, *Gs, *SAS, *SBS, *Cm, *PAP, *PAPn;
   double* kinv = nullptr;  // 1 / diag(K) for the current solve (n)
+  int slice_boost = 0;     // 7 once a solve in an emulated form has stalled
   int *cexp, *zexp;  // column balance exponents of S, and all zeros
   void* gwork = nullptr;
   int64_t gwork_bytes = 0;
@@ -177,7 +178,12 @@ int gemm_mode(const lobpcg_ctx* h) {
              ? h->opt.gemm_mode
              : 0;
 }
-int slices(const lobpcg_ctx* h) { return h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : 6; }
+// Slices of the emulated contractions: the option (default 6), raised to 7
+// for the rest of a solve when the iteration stalls (see solve_impl).
+int slices(const lobpcg_ctx* h) {
+  const int sl = h->opt.ozaki_slices > 0 ? h->opt.ozaki_slices : 6;
+  return std::max(sl, h->slice_boost);
+}
 
 int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   const int64_t n = h->n;
@@ -444,6 +450,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   if (!lambda || !Xout || ldx < k) return h->fail(LOBPCG_ERR_ARG, "bad output buffers");
   if (X0 && ldx0 < nx) return h->fail(LOBPCG_ERR_ARG, "ldx0 < block width");
   if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
+  h->slice_boost = 0;
   int rc = ensure_workspace(h, nx);
   if (rc) return h->fail(rc, "workspace allocation failed");
   const auto t_start = std::chrono::steady_clock::now();
@@ -455,6 +462,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats = lobpcg_stats_t{};
   h->stats.n_x = nx;
   h->stats.flip_iteration = -1;
+  h->stats.slice_escalation_iteration = -1;
   const int64_t ld = h->ld;
   const int s = h->opt.omega_rows > 0 ? h->opt.omega_rows : 16;
   const int maxit = h->opt.maxit > 0 ? h->opt.maxit : 2000;
@@ -528,6 +536,9 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   int64_t nc = 0;
   int np = 0;
   bool use_ortho = false, refresh_next = false;
+  constexpr int64_t kStallWindow = 400;
+  int64_t stall_nc = -1, stall_it = 0;
+  double stall_be = INFINITY;
   int64_t it = 0;
   int status = LOBPCG_OK;
   // W (or R for a callback preconditioner) of columns c0 .. nx-1, then locking.
@@ -677,6 +688,23 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       if ((rc = to_host(h, be_h.data(), h->be, nx - nc))) return rc;
       const int64_t ncn = std::max(nc, nc + leading_converged(be_h.data(), nx - nc, tol));
       refresh_next = ncn > nc;
+      // Stall guard of the emulated forms: when over kStallWindow iterations
+      // no column converges and the leading unconverged backward error has
+      // not dropped by 10 %, the contractions have reached their accuracy
+      // floor for this spectrum; the rest of the solve runs with 7 slices
+      // (2^-52 per operand block) and the implicit products are refreshed.
+      if (gemm_mode(h) && h->slice_boost == 0 && slices(h) < 7) {
+        if (ncn != stall_nc || it - stall_it >= kStallWindow) {
+          if (ncn == stall_nc && !(be_h[0] < 0.9 * stall_be) && it - stall_it >= kStallWindow) {
+            h->slice_boost = 7;
+            h->stats.slice_escalation_iteration = it;
+            refresh_next = true;
+          }
+          stall_nc = ncn;
+          stall_it = it;
+          stall_be = be_h[std::min<int64_t>(ncn - nc, nx - nc - 1)];  // leading unconverged
+        }
+      }
       if ((rc = finish_w(nc, ncn))) return h->fail(rc, "preconditioner callback failed");
       nc = ncn;
     }

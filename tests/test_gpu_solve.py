@@ -302,3 +302,22 @@ def test_reduced_c3_c4_against_oracle_and_dense(mode, name, kw):
     # tcgen05 emulation (2^-44 per product, n_s-long sums) ~4e-12 here
     _check_pairs(p, lam, X, be, r.normA, r.normB,
                  tol_orth=1e-12 if mode == "f64" else 1e-11)
+
+
+def test_c5_default_form_escalates_and_converges():
+    """c5 at full size (512^2 Laplacian + V, k = 32, tol 1e-8) in the default
+    form: the 6-slice tcgen05 contractions stall short of tol on this
+    spectrum, the stall guard raises them to 7 slices, and the solve
+    converges: explicit FP64 residuals of Eq. (9) on the host and X^T X = I."""
+    torch = torch_cuda()
+    p = synth.make_problem("lap2d_512_V", seed=0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s = gb.Solver(gemm_mode="ozaki_tc", maxit=6000)
+    s.set_operator(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val))
+    lam, X, it, be, rc = s.solve(p.k, 1e-8, device=True, raise_on_error=False)
+    st = s.stats()
+    s.close()
+    assert rc == gb.LOBPCG_OK
+    assert st["slice_escalation_iteration"] > 0
+    _check_pairs(p, lam.cpu().numpy(), X.cpu().numpy(), be.cpu().numpy(), st["norm_a"],
+                 st["norm_b"], tol_orth=1e-11)
