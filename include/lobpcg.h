@@ -128,9 +128,15 @@ int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, void* stream);
 /* Set the pencil.  A: CSR (n, A_nnz).  B: either CSR (B_rowptr != NULL), or a
  * diagonal (B_diag != NULL, n values), or the identity (both NULL).  `mem`
  * says whether the arrays are host or device pointers; they are copied.
- * Resets the preconditioner to Jacobi K = diag(A) (Algorithm 1, Eq. 2).
- * Errors: LOBPCG_ERR_ARG for n <= 0, a zero diagonal entry of A (Jacobi), or
- * nnz >= 2^31. */
+ * Resets the preconditioner to Jacobi K = diag(A) (Algorithm 1, Eq. 2); when
+ * diag(A) has a zero entry K = I instead, the call returns LOBPCG_OK and
+ * lobpcg_last_error says so.
+ * Errors: LOBPCG_ERR_ARG for n outside 1..2^31, nnz outside 0..2^31-1, B
+ * given both ways, a non-positive diagonal B, and, for host arrays (checked
+ * before anything is copied), a CSR whose rowptr does not run monotonically
+ * from 0 to nnz or whose column indices leave 0..n-1 (device arrays are
+ * trusted).  After any error the handle holds no operator: lobpcg_solve and
+ * lobpcg_eig_adjoint return LOBPCG_ERR_ARG until an operator is set. */
 int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
                         const int32_t* A_col, const double* A_val, int64_t A_nnz,
                         const int32_t* B_rowptr, const int32_t* B_col,
@@ -138,7 +144,8 @@ int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
                         int mem);
 
 /* Diagonal preconditioner K = diag(kdiag) (n values, `mem` as above);
- * kdiag == NULL restores K = diag(A); a negative `mem` selects K = I. */
+ * kdiag == NULL restores K = diag(A); a negative `mem` selects K = I.
+ * Host values must be positive (LOBPCG_ERR_ARG otherwise). */
 int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int mem);
 
 /* General preconditioner through a callback (see lobpcg_precond_fn). */

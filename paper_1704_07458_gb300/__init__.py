@@ -85,27 +85,57 @@ class Solver:
         if rc != LOBPCG_OK:
             raise LobpcgError(rc, f"{what}: {lobpcg_last_error(self.h)}")
 
+    @staticmethod
+    def _arg(x, mem, dtype, name):
+        """Marshal one array argument: host arrays become contiguous numpy of
+        `dtype`; device tensors must already be contiguous CUDA tensors of
+        that dtype (the library reads them as raw int32 / float64 memory)."""
+        if x is None:
+            return None
+        if mem == LOBPCG_MEM_HOST:
+            if hasattr(x, "is_cuda"):
+                if x.is_cuda:
+                    raise ValueError(f"{name}: a CUDA tensor among host arguments")
+                x = x.detach().numpy()
+            return np.ascontiguousarray(x, dtype=dtype)
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            raise ValueError(f"{name}: a host array among device arguments")
+        want = {np.int32: "torch.int32", np.float64: "torch.float64"}[dtype]
+        if str(x.dtype) != want:
+            raise TypeError(f"{name}: device tensor must be {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: device tensor must be contiguous")
+        return x
+
     def set_operator(self, rowptr, col, val, b_diag=None, b_csr=None):
         mem = self._mem(val)
         n = len(rowptr) - 1
-        args = dict(B_diag=b_diag)
+        rowptr = self._arg(rowptr, mem, np.int32, "rowptr")
+        col = self._arg(col, mem, np.int32, "col")
+        val = self._arg(val, mem, np.float64, "val")
+        if len(col) != len(val):
+            raise ValueError("col and val differ in length")
+        args = dict(B_diag=self._arg(b_diag, mem, np.float64, "b_diag"))
         if b_csr is not None:
-            args = dict(B_rowptr=b_csr[0], B_col=b_csr[1], B_val=b_csr[2], B_nnz=len(b_csr[2]))
-        if mem == LOBPCG_MEM_HOST:
-            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
-            col = np.ascontiguousarray(col, dtype=np.int32)
-            val = np.ascontiguousarray(val, dtype=np.float64)
-            if b_diag is not None:
-                args["B_diag"] = np.ascontiguousarray(b_diag, dtype=np.float64)
+            brp = self._arg(b_csr[0], mem, np.int32, "b_csr rowptr")
+            bcol = self._arg(b_csr[1], mem, np.int32, "b_csr col")
+            bval = self._arg(b_csr[2], mem, np.float64, "b_csr val")
+            if len(brp) != n + 1 or len(bcol) != len(bval):
+                raise ValueError("b_csr does not match the size of A")
+            args = dict(B_rowptr=brp, B_col=bcol, B_val=bval, B_nnz=len(bval))
+        elif b_diag is not None and len(args["B_diag"]) != n:
+            raise ValueError("b_diag must have n entries")
         self._keep = (rowptr, col, val, args)
+        self.n = 0
         rc = lobpcg_set_operator(self.h, n, rowptr, col, val, len(val), mem=mem, **args)
         self._check(rc, "set_operator")
         self.n = n
 
     def set_precond_diag(self, kdiag):
         mem = self._mem(kdiag)
-        if kdiag is not None and mem == LOBPCG_MEM_HOST:
-            kdiag = np.ascontiguousarray(kdiag, dtype=np.float64)
+        kdiag = self._arg(kdiag, mem, np.float64, "kdiag")
+        if kdiag is not None and len(kdiag) != self.n:
+            raise ValueError("kdiag must have n entries")
         self._check(lobpcg_set_precond_diag(self.h, kdiag, mem), "set_precond_diag")
 
     def set_precond_identity(self):
@@ -131,8 +161,9 @@ class Solver:
         mem_in = self._mem(X0)
         ldx0 = 0
         if X0 is not None:
-            if mem_in == LOBPCG_MEM_HOST:
-                X0 = np.ascontiguousarray(X0, dtype=np.float64)
+            X0 = self._arg(X0, mem_in, np.float64, "X0")
+            if X0.ndim != 2 or X0.shape[0] != n:
+                raise ValueError("X0 must be n x n_x")
             ldx0 = X0.shape[1]
         if device:
             import torch
@@ -162,15 +193,20 @@ class Solver:
         b_args = self._keep[3]
         b_len = (len(b_args["B_val"]) if "B_val" in b_args else
                  (n if b_args.get("B_diag") is not None else 0))
+        X = self._arg(X, mem, np.float64, "X")
+        lam = self._arg(lam, mem, np.float64, "lam")
+        glam = self._arg(glam, mem, np.float64, "glam")
+        G = self._arg(G, mem, np.float64, "G")
+        if X.ndim != 2 or X.shape[0] != n or X.shape[1] < k or len(lam) < k:
+            raise ValueError("X must be n x (>= k) and lam hold >= k values")
+        if (glam is not None and len(glam) < k) or (
+                G is not None and (G.ndim != 2 or G.shape[0] != n or G.shape[1] < k)):
+            raise ValueError("glam must hold >= k values and G be n x (>= k)")
         if mem == LOBPCG_MEM_DEVICE:
             import torch
             gA = torch.empty(nnz_a, dtype=torch.float64, device="cuda")
             gB = torch.empty(b_len, dtype=torch.float64, device="cuda") if b_len else None
         else:
-            X = np.ascontiguousarray(X, dtype=np.float64)
-            lam = np.ascontiguousarray(lam, dtype=np.float64)
-            glam = None if glam is None else np.ascontiguousarray(glam, dtype=np.float64)
-            G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
             gA = np.empty(nnz_a)
             gB = np.empty(b_len) if b_len else None
         rc, its = lobpcg_eig_adjoint(self.h, k, lam, X, X.shape[1], glam, G,

@@ -449,6 +449,9 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   if (3 * nx > 6144) return h->fail(LOBPCG_ERR_ARG, "block too wide (3 n_x > 6144)");
   if (!lambda || !Xout || ldx < k) return h->fail(LOBPCG_ERR_ARG, "bad output buffers");
   if (X0 && ldx0 < nx) return h->fail(LOBPCG_ERR_ARG, "ldx0 < block width");
+  for (int m : {mem_in, mem_out})
+    if (m != LOBPCG_MEM_HOST && m != LOBPCG_MEM_DEVICE)
+      return h->fail(LOBPCG_ERR_ARG, "memory kinds must be LOBPCG_MEM_HOST or LOBPCG_MEM_DEVICE");
   if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
   h->slice_boost = 0;
   int rc = ensure_workspace(h, nx);
@@ -774,7 +777,11 @@ __global__ void csr_diag_kernel(int64_t n, const int32_t* rp, const int32_t* ci,
 int copy_in(lobpcg_ctx* h, void** dst, const void* src, size_t bytes, int mem) {
   if (*dst) cudaFree(*dst);
   *dst = nullptr;
-  if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return LOBPCG_ERR_OOM;
+  }
   LOB_CUDA_OK(cudaMemcpyAsync(*dst, src, bytes,
                               mem == LOBPCG_MEM_DEVICE ? cudaMemcpyDeviceToDevice
                                                        : cudaMemcpyHostToDevice,
@@ -811,6 +818,9 @@ int adjoint_impl(lobpcg_ctx* h, int64_t k64, const double* lambda, const double*
   if (!lambda || !Xin || ldx < k64 || !gA) return h->fail(LOBPCG_ERR_ARG, "bad arguments");
   if (Gin && ldg < k64) return h->fail(LOBPCG_ERR_ARG, "ldg < k");
   if (h->b_kind != 0 && !gB) return h->fail(LOBPCG_ERR_ARG, "gB is needed when B is not I");
+  for (int m : {mem_in, mem_out})
+    if (m != LOBPCG_MEM_HOST && m != LOBPCG_MEM_DEVICE)
+      return h->fail(LOBPCG_ERR_ARG, "memory kinds must be LOBPCG_MEM_HOST or LOBPCG_MEM_DEVICE");
   if (h->k_kind == 3 && !h->cb) return h->fail(LOBPCG_ERR_ARG, "no callback set");
   const int k = (int)k64;
   if (!(cg_tol > 0)) cg_tol = 1e-10;
@@ -1023,18 +1033,43 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
                                       const double* B_val, int64_t B_nnz, const double* B_diag,
                                       int mem) {
   if (!h) return LOBPCG_ERR_ARG;
-  if (n <= 0 || n > (int64_t)1 << 31) return h->fail(LOBPCG_ERR_ARG, "n out of range");
+  // Any failure leaves the handle without an operator, so that a later solve
+  // or adjoint returns LOBPCG_ERR_ARG instead of using stale, freed or
+  // partial buffers.
+  auto drop = [h](int code, const char* msg) {
+    h->free_ws();
+    h->release_op();
+    h->n = h->A_nnz = h->B_nnz = 0;
+    h->b_kind = 0;
+    h->b_cond = 1.0;
+    h->k_kind = 0;
+    return h->fail(code, msg);
+  };
+  if (n <= 0 || n > (int64_t)1 << 31) return drop(LOBPCG_ERR_ARG, "n out of range");
   if (!A_rowptr || !A_col || !A_val || A_nnz < 0 || A_nnz >= ((int64_t)1 << 31))
-    return h->fail(LOBPCG_ERR_ARG, "bad A");
+    return drop(LOBPCG_ERR_ARG, "bad A");
   if (B_rowptr && (!B_col || !B_val || B_nnz < 0 || B_nnz >= ((int64_t)1 << 31)))
-    return h->fail(LOBPCG_ERR_ARG, "bad B");
-  if (B_rowptr && B_diag) return h->fail(LOBPCG_ERR_ARG, "give B as CSR or diagonal, not both");
+    return drop(LOBPCG_ERR_ARG, "bad B");
+  if (B_rowptr && B_diag) return drop(LOBPCG_ERR_ARG, "give B as CSR or diagonal, not both");
   if (mem == LOBPCG_MEM_HOST) {
-    if (A_rowptr[0] != 0 || A_rowptr[n] != A_nnz) return h->fail(LOBPCG_ERR_ARG, "bad A rowptr");
-    for (int64_t i = 0; i < n; ++i)
-      if (A_rowptr[i + 1] < A_rowptr[i]) return h->fail(LOBPCG_ERR_ARG, "A rowptr not monotone");
-    for (int64_t p = 0; p < A_nnz; ++p)
-      if (A_col[p] < 0 || A_col[p] >= n) return h->fail(LOBPCG_ERR_ARG, "A column out of range");
+    // host arrays are checked before anything is copied: the kernels index
+    // through rowptr and col without bounds checks
+    auto csr_ok = [n](const int32_t* rp, const int32_t* ci, int64_t nnz) {
+      if (rp[0] != 0 || rp[n] != nnz) return false;
+      for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return false;
+      for (int64_t p = 0; p < nnz; ++p)
+        if (ci[p] < 0 || ci[p] >= n) return false;
+      return true;
+    };
+    if (!csr_ok(A_rowptr, A_col, A_nnz)) return drop(LOBPCG_ERR_ARG, "A is not a valid n x n CSR");
+    if (B_rowptr && !csr_ok(B_rowptr, B_col, B_nnz))
+      return drop(LOBPCG_ERR_ARG, "B is not a valid n x n CSR");
+    if (B_diag)
+      for (int64_t i = 0; i < n; ++i)
+        if (!(B_diag[i] > 0)) return drop(LOBPCG_ERR_ARG, "diagonal B must be positive");
+  } else if (mem != LOBPCG_MEM_DEVICE) {
+    return drop(LOBPCG_ERR_ARG, "mem must be LOBPCG_MEM_HOST or LOBPCG_MEM_DEVICE");
   }
   h->free_ws();
   h->release_op();
@@ -1044,7 +1079,7 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
   if ((rc = copy_in(h, (void**)&h->A_rp, A_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
       (rc = copy_in(h, (void**)&h->A_ci, A_col, A_nnz * sizeof(int32_t), mem)) ||
       (rc = copy_in(h, (void**)&h->A_v, A_val, A_nnz * sizeof(double), mem)))
-    return h->fail(rc, "copying A failed");
+    return drop(rc, "copying A failed");
   h->b_kind = 0;
   h->b_cond = 1.0;
   if (B_rowptr) {
@@ -1053,26 +1088,28 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
     if ((rc = copy_in(h, (void**)&h->B_rp, B_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
         (rc = copy_in(h, (void**)&h->B_ci, B_col, B_nnz * sizeof(int32_t), mem)) ||
         (rc = copy_in(h, (void**)&h->B_v, B_val, B_nnz * sizeof(double), mem)))
-      return h->fail(rc, "copying B failed");
+      return drop(rc, "copying B failed");
   } else if (B_diag) {
     h->b_kind = 1;
     if ((rc = copy_in(h, (void**)&h->b_diag, B_diag, n * sizeof(double), mem)))
-      return h->fail(rc, "copying B failed");
+      return drop(rc, "copying B failed");
     std::vector<double> b(n);
     if (cudaMemcpyAsync(b.data(), h->b_diag, n * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
             cudaSuccess ||
         cudaStreamSynchronize(h->st) != cudaSuccess)
-      return h->fail(LOBPCG_ERR_CUDA, "reading B failed");
+      return drop(LOBPCG_ERR_CUDA, "reading B failed");
     double lo = INFINITY, hi = 0.0;
     for (double x : b) {
       lo = std::min(lo, std::fabs(x));
       hi = std::max(hi, std::fabs(x));
-      if (!(x > 0)) return h->fail(LOBPCG_ERR_ARG, "diagonal B must be positive");
+      if (!(x > 0)) return drop(LOBPCG_ERR_ARG, "diagonal B must be positive");
     }
     h->b_cond = hi / lo;
   }
-  if (cudaMalloc(&h->adiag, n * sizeof(double)) != cudaSuccess)
-    return h->fail(LOBPCG_ERR_OOM, "allocation failed");
+  if (cudaMalloc(&h->adiag, n * sizeof(double)) != cudaSuccess) {
+    h->adiag = nullptr;
+    return drop(LOBPCG_ERR_OOM, "allocation failed");
+  }
   csr_diag_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, h->st>>>(n, h->A_rp, h->A_ci, h->A_v,
                                                                  h->adiag);
   ++g_launches;
@@ -1080,7 +1117,7 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
   if (cudaMemcpyAsync(d.data(), h->adiag, n * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
           cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess)
-    return h->fail(LOBPCG_ERR_CUDA, "reading diag(A) failed");
+    return drop(LOBPCG_ERR_CUDA, "reading diag(A) failed");
   h->k_kind = 0;
   for (double x : d)
     if (x == 0.0) {
@@ -1102,8 +1139,16 @@ LOBPCG_EXPORT int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int m
     h->k_kind = 0;
     return LOBPCG_OK;
   }
+  if (mem != LOBPCG_MEM_HOST && mem != LOBPCG_MEM_DEVICE)
+    return h->fail(LOBPCG_ERR_ARG, "mem must be negative, LOBPCG_MEM_HOST or LOBPCG_MEM_DEVICE");
+  if (mem == LOBPCG_MEM_HOST)
+    for (int64_t i = 0; i < h->n; ++i)
+      if (!(kdiag[i] > 0)) return h->fail(LOBPCG_ERR_ARG, "diagonal K must be positive");
   int rc = copy_in(h, (void**)&h->kdiag, kdiag, h->n * sizeof(double), mem);
-  if (rc) return h->fail(rc, "copying K failed");
+  if (rc) {
+    h->k_kind = 0;
+    return h->fail(rc, "copying K failed");
+  }
   h->k_kind = 1;
   return LOBPCG_OK;
 }

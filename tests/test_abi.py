@@ -79,6 +79,55 @@ def test_host_side_argument_errors_without_gpu(lib):
     assert lib.lobpcg_last_error(None) == b"null handle"
 
 
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor: the attributes the binding inspects."""
+
+    def __init__(self, dtype, contiguous=True):
+        self.is_cuda = True
+        self.dtype = dtype
+        self._c = contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_binding_marshals_and_refuses_misread_arrays():
+    """Host arrays are converted to the ABI's int32 / float64; device tensors
+    of another dtype, non-contiguous ones, and host / device mixes are refused
+    before the library sees a pointer."""
+    import numpy as np
+    import torch
+    H, D = gb.LOBPCG_MEM_HOST, gb.LOBPCG_MEM_DEVICE
+    a = gb.Solver._arg(np.arange(5, dtype=np.int64), H, np.int32, "col")
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    b = gb.Solver._arg(torch.arange(6.0).reshape(2, 3).t(), H, np.float64, "X0")
+    assert b.dtype == np.float64 and b.flags.c_contiguous and b.shape == (3, 2)
+    assert gb.Solver._arg(None, D, np.float64, "x") is None
+    ok = _FakeDeviceTensor("torch.int32")
+    assert gb.Solver._arg(ok, D, np.int32, "col") is ok
+    with pytest.raises(TypeError):
+        gb.Solver._arg(_FakeDeviceTensor("torch.int64"), D, np.int32, "col")
+    with pytest.raises(TypeError):
+        gb.Solver._arg(_FakeDeviceTensor("torch.float32"), D, np.float64, "val")
+    with pytest.raises(ValueError):
+        gb.Solver._arg(_FakeDeviceTensor("torch.float64", contiguous=False), D, np.float64, "X0")
+    with pytest.raises(ValueError):
+        gb.Solver._arg(np.zeros(3), D, np.float64, "val")
+    with pytest.raises(ValueError):
+        gb.Solver._arg(_FakeDeviceTensor("torch.float64"), H, np.float64, "val")
+    # shape checks run before any library call (no handle is needed for them)
+    s = object.__new__(gb.Solver)
+    s.h, s.n = None, 0
+    with pytest.raises(ValueError):
+        s.set_operator(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0]))
+    with pytest.raises(ValueError):
+        s.set_operator(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0, 1.0]),
+                       b_diag=np.ones(3))
+    with pytest.raises(ValueError):
+        s.set_operator(np.array([0, 1, 2]), np.array([0, 1]), np.array([1.0, 1.0]),
+                       b_csr=(np.array([0, 1]), np.array([0]), np.array([1.0])))
+
+
 def test_binding_has_no_cpu_fallback():
     """The product package never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_1704_07458_gb300")

@@ -173,6 +173,58 @@ def test_breakdown_not_converged_and_bad_args():
     s.close()
 
 
+def test_invalid_operator_is_rejected_and_dropped():
+    """Host CSR arrays, diagonals and memory kinds are checked before anything
+    is copied; after a rejected operator the handle holds none, so a solve is
+    refused (no device work on stale or partial buffers); a valid operator
+    set afterwards solves normally."""
+    torch = torch_cuda()
+    p = synth.make_problem("lap2d_32")
+    A = p.A
+    H = gb.LOBPCG_MEM_HOST
+    s = gb.Solver(gemm_mode="f64")
+    bad_col = A.col.copy()
+    bad_col[5] = A.n
+    bad_rp = A.rowptr.copy()
+    bad_rp[3], bad_rp[4] = bad_rp[4], bad_rp[3]
+    zero_b = np.ones(A.n)
+    zero_b[7] = 0.0
+    cases = [
+        (A.rowptr, bad_col, A.val, {}, H, "CSR"),
+        (bad_rp, A.col, A.val, {}, H, "CSR"),
+        (A.rowptr, A.col, A.val, dict(B_rowptr=A.rowptr, B_col=bad_col, B_val=A.val,
+                                      B_nnz=A.nnz), H, "CSR"),
+        (A.rowptr, A.col, A.val, dict(B_diag=zero_b), H, "positive"),
+        (A.rowptr, A.col, A.val, dict(B_diag=np.ones(A.n), B_rowptr=A.rowptr, B_col=A.col,
+                                      B_val=A.val, B_nnz=A.nnz), H, "not both"),
+        (A.rowptr, A.col, A.val, {}, 7, "mem"),
+    ]
+    for rp, ci, v, b, mem, msg in cases:
+        s.set_operator(A.rowptr, A.col, A.val)  # a valid operator first
+        rc = gb.lobpcg_set_operator(s.h, A.n, rp, ci, v, A.nnz, mem=mem, **b)
+        assert rc == gb.LOBPCG_ERR_ARG, msg
+        assert msg in gb.lobpcg_last_error(s.h), msg
+        lam, X, it, be, rc = s.solve(p.k, p.tol, raise_on_error=False)
+        assert rc == gb.LOBPCG_ERR_ARG
+        assert "no operator" in gb.lobpcg_last_error(s.h)
+    # the binding refuses device tensors the library would misread
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with pytest.raises(TypeError):
+        s.set_operator(dev(A.rowptr), dev(A.col.astype(np.int64)), dev(A.val))
+    with pytest.raises(ValueError):
+        s.set_operator(A.rowptr, A.col, dev(A.val))
+    # a non-positive host K is refused and Jacobi stays in place
+    s.set_operator(A.rowptr, A.col, A.val)
+    kbad = A.diagonal().copy()
+    kbad[0] = -1.0
+    assert gb.lobpcg_set_precond_diag(s.h, kbad, H) == gb.LOBPCG_ERR_ARG
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, synth.block_width(p.k))
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0)
+    assert rc == gb.LOBPCG_OK
+    np.testing.assert_allclose(lam, p.closed_form[:p.k], rtol=1e-10)
+    s.close()
+
+
 class _DevView:
     """Zero-copy view of library-owned device memory (CUDA array interface)."""
 
