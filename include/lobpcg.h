@@ -47,7 +47,12 @@ typedef enum {
 typedef enum { LOBPCG_MEM_HOST = 0, LOBPCG_MEM_DEVICE = 1 } lobpcg_mem;
 
 /* Arithmetic used for the n-scaled dense contractions (Gram S^T Y and basis
- * update S C).  Both give FP64-accurate results; see lobpcg_gram. */
+ * update S C).  F64 rounds like any FP64 dot product.  The emulated modes cut
+ * each FP64 input of a 64-long chunk into `slices` exact BF16 digits against
+ * the exponent bound of its chunk row or column; each term is then exact to
+ * about 2^-44 (6 slices) or 2^-56 (7) relative to those bounds, and the sums
+ * are accumulated in double-float.  Everything else (projected pencils,
+ * Algorithm 7, norms, Eq. 9) runs in FP64 in every mode. */
 typedef enum {
   LOBPCG_GEMM_F64 = 0,      /* plain FP64 fused multiply-add on the CUDA cores */
   LOBPCG_GEMM_OZAKI = 1,    /* FP64 emulated by exact BF16 splits, warp-level mma.sync */
