@@ -141,7 +141,9 @@ int lobpcg_create(lobpcg_t* out, const lobpcg_options_t* opts, void* stream);
  * before anything is copied), a CSR whose rowptr does not run monotonically
  * from 0 to nnz or whose column indices leave 0..n-1 (device arrays are
  * trusted).  After any error the handle holds no operator: lobpcg_solve and
- * lobpcg_eig_adjoint return LOBPCG_ERR_ARG until an operator is set. */
+ * lobpcg_eig_adjoint return LOBPCG_ERR_ARG until an operator is set.  The one
+ * exception is a call made while another CUDA device than the handle's is
+ * current: it returns LOBPCG_ERR_ARG and changes nothing. */
 int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
                         const int32_t* A_col, const double* A_val, int64_t A_nnz,
                         const int32_t* B_rowptr, const int32_t* B_col,

@@ -1033,7 +1033,10 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
                                       const double* B_val, int64_t B_nnz, const double* B_diag,
                                       int mem) {
   if (!h) return LOBPCG_ERR_ARG;
-  // Any failure leaves the handle without an operator, so that a later solve
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return h->fail(LOBPCG_ERR_ARG, "handle belongs to another device");
+  // Any other failure leaves the handle without an operator, so that a later solve
   // or adjoint returns LOBPCG_ERR_ARG instead of using stale, freed or
   // partial buffers.
   auto drop = [h](int code, const char* msg) {
@@ -1131,6 +1134,9 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
 LOBPCG_EXPORT int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int mem) {
   if (!h) return LOBPCG_ERR_ARG;
   if (h->n <= 0) return h->fail(LOBPCG_ERR_ARG, "set the operator first");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return h->fail(LOBPCG_ERR_ARG, "handle belongs to another device");
   if (mem < 0) {
     h->k_kind = 2;
     return LOBPCG_OK;
