@@ -361,11 +361,12 @@ def test_c5_default_form_converges():
     form (6-slice tcgen05 contractions, with the stall guard that continues
     a flat-lined solve with 7 slices) converges: explicit FP64 residuals of
     Eq. (9) on the host, and X^T X = I to 1e-8.  That bound is looser than
-    c2's 1e-10: the Cholesky-based Rayleigh-Ritz of Algorithm 7 makes X
-    orthonormal in the metric of the computed Gram, whose 2^-44 error is
-    amplified by cond(R)^2 (up to 3.6e4^2 below the tau_skip switch); on this
-    spectrum the measured deviation is 5.1e-9, among the nearly degenerate
-    localised states 28-31."""
+    c2's 1e-10: the projected pencil takes X^T B X = I, X^T B P = 0 and
+    P^T B P = I from the identities (12)-(14), the updates' 2^-44 rounding
+    departs from them, and the Cholesky branch of Algorithm 7 multiplies that
+    mismatch through C every iteration; over this spectrum's ~2000
+    iterations the measured deviation is 5.1e-9, among the nearly
+    degenerate localised states 28-31."""
     torch = torch_cuda()
     p = synth.make_problem("lap2d_512_V", seed=0)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
