@@ -23,7 +23,9 @@ def jacobi_eigh(A, tol=1e-15, max_sweeps=60):
     """All eigenpairs of a real symmetric matrix by cyclic Jacobi rotations.
 
     Each (p, q) rotation zeroes A[p, q] with the stable choice of tangent
-    t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq).
+    t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq),
+    the square root taken as hypot(1, tau) so that a huge tau gives the
+    small-angle tangent 1 / (2 tau) rather than an overflow.
     Sweeps repeat until the off-diagonal Frobenius norm is below
     tol * ||A||_F.  Returns (w ascending, V) with A V = V diag(w).
     """
@@ -43,7 +45,10 @@ def jacobi_eigh(A, tol=1e-15, max_sweeps=60):
                 if apq == 0.0:
                     continue
                 tau = (A[q, q] - A[p, p]) / (2.0 * apq)
-                t = (1.0 if tau >= 0 else -1.0) / (abs(tau) + np.sqrt(1.0 + tau * tau))
+                # sqrt(1 + tau^2) as hypot(1, tau): for |tau| beyond 1e154 the
+                # square overflows, and the tangent must tend to the small-angle
+                # value 1 / (2 tau) instead of 0 (Golub & Van Loan, Sec. 8.5.2)
+                t = (1.0 if tau >= 0 else -1.0) / (abs(tau) + np.hypot(1.0, tau))
                 c = 1.0 / np.sqrt(1.0 + t * t)
                 s = t * c
                 # A <- J^T A J with J the rotation in the (p, q) plane

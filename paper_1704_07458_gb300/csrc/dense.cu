@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(256) cluster_jacobi_kernel(int n, const double
           if (apq == 0.0) continue;
           // rotation zeroing M[p][q] (Golub & Van Loan, Sec. 8.5.2)
           const double tau = (M[q][q] - M[p][p]) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          // hypot(1, tau): no overflow of tau^2 for tiny a_pq (small-angle t = 1/(2 tau))
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
           const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
           __syncwarp();
           for (int k = lane; k < m; k += 32) {  // columns p, q

@@ -25,6 +25,22 @@ def test_jacobi_1d_laplacian_closed_form(n):
     np.testing.assert_allclose(A @ V, V * w, atol=1e-12)
 
 
+def test_jacobi_tiny_coupling_small_angle():
+    """A coupling of 1e-160 gives tau = 5e159, whose square overflows: the
+    rotation must still take the small-angle tangent 1/(2 tau) = 1e-160, so
+    the eigenvector of eigenvalue 2 carries 1e-160 in its first entry
+    ((A - 2 I) v = 0 with v = (e, 1): e = 1e-160 / (2 - 1))."""
+    c = 1e-160
+    A = np.array([[1.0, c], [c, 2.0]])
+    with np.errstate(over="raise", invalid="raise"):
+        # tol = 0: the sweep may not stop before rotating the tiny coupling away
+        w, V = dense.jacobi_eigh(A, tol=0.0)
+    np.testing.assert_array_equal(w, [1.0, 2.0])
+    v = V[:, 1] * np.sign(V[1, 1])
+    assert v[1] == 1.0
+    np.testing.assert_allclose(v[0], c, rtol=1e-14)
+
+
 def test_jacobi_prescribed_spectrum():
     n = 30
     Q = _householder_orthogonal(n, 1)
