@@ -117,6 +117,15 @@ typedef struct {
    * leading backward error flat over 400 iterations) raised the contractions
    * to 7 slices for the rest of the solve; -1 never */
   int64_t slice_escalation_iteration;
+  /* algorithmic HBM bytes of the contractions over the solve, each operand
+   * block read once and each output written once (8-byte words): Gram
+   * 8 n (p + q); update 8 n (s + m), plus 8 n m when Y0 is read */
+  double gram_bytes, update_bytes;
+  /* ||X^T B X - I||_F of the first k returned columns, from explicit FP64
+   * products after the exit certification (-1 when not computed) */
+  double orth_error;
+  /* host waits on the stream (device scalars read back) during the solve */
+  int64_t host_syncs;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.

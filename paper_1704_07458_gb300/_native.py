@@ -86,6 +86,10 @@ class lobpcg_stats_t(ctypes.Structure):
         ("eig_calls", ctypes.c_int64),
         ("eig_fallbacks", ctypes.c_int64),
         ("slice_escalation_iteration", ctypes.c_int64),
+        ("gram_bytes", ctypes.c_double),
+        ("update_bytes", ctypes.c_double),
+        ("orth_error", ctypes.c_double),
+        ("host_syncs", ctypes.c_int64),
     ]
 
     def as_dict(self):

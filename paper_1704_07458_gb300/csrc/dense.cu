@@ -506,6 +506,7 @@ static int copy_mat(DenseLayer& L, int rows, int cols, const double* S, int lds,
 static int to_host(DenseLayer& L, double* dst, const void* src, size_t bytes) {
   LOB_CUDA_OK(cudaMemcpyAsync(L.host, src, bytes, cudaMemcpyDeviceToHost, L.st));
   LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  ++L.syncs;
   memcpy(dst, L.host, bytes);
   return LOBPCG_OK;
 }
@@ -573,6 +574,7 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
     LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                 L.st));
     LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+    ++L.syncs;
     const double dnew = L.host[0];
     normA = L.host[1];
     if (!std::isfinite(dnew)) {
@@ -599,6 +601,7 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
                               L.st));
   LOB_CUDA_OK(cudaMemcpyAsync(L.host + n + 1, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
   LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  ++L.syncs;
   int info;
   memcpy(&info, L.host + n + 1, sizeof(int));
   const double* d = L.host;
@@ -643,6 +646,7 @@ static int syevd(DenseLayer& L, bool vectors, int n, double* A, int lda) {
   double worst = 0.0;
   LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, L.st));
   LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  ++L.syncs;
   worst = L.host[0];
   if (!(worst <= 8.0 * std::sqrt((double)n) * kEps * normA)) {
     ++L.eig_fallbacks;
@@ -764,6 +768,7 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
   LOB_CUDA_OK(cudaMemcpyAsync(L.host, L.ev, nx * sizeof(double), cudaMemcpyDeviceToHost, L.st));
   LOB_CUDA_OK(cudaMemcpyAsync(L.host + nx, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
   LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  ++L.syncs;
   int info;
   memcpy(&info, L.host + nx, sizeof(int));
   const double lo = L.host[0], hi = L.host[nx - 1];
@@ -811,6 +816,7 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
     SOL_OK(cusolverDnDpotrf(L.sol, CUBLAS_FILL_MODE_UPPER, ns, Rm, ld, L.work, L.lwork, L.info));
     LOB_CUDA_OK(cudaMemcpyAsync(L.host + 1, L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
     LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+    ++L.syncs;
     int info;
     memcpy(&info, L.host + 1, sizeof(int));
     if (info != 0) {

@@ -132,6 +132,7 @@ struct lobpcg_ctx {
   int64_t uwork_bytes = 0;
   void* rwork = nullptr;
   double* hbuf = nullptr;  // pinned host
+  int64_t syncs = 0;       // host waits on the stream (stats.host_syncs)
   DenseLayer dense;
   PhaseTimer timer;
 
@@ -260,6 +261,7 @@ int gram(lobpcg_ctx* h, const SegList& U, const SegList& V, double* G, int64_t l
   Scoped sc(h->timer, PH_GRAM);
   h->stats.gram_calls++;
   h->stats.gram_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg];
+  h->stats.gram_bytes += 8.0 * h->n * (U.off[U.nseg] + V.off[V.nseg]);
   if (gemm_mode(h)) {
     const int sl = std::max(slices(h), min_slices);
     h->stats.gram_tensor_flops += 2.0 * h->n * U.off[U.nseg] * V.off[V.nseg] * sl * (sl + 1) / 2;
@@ -281,6 +283,7 @@ int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m,
   Scoped sc(h->timer, PH_UPDATE);
   h->stats.update_calls++;
   h->stats.update_flops += 2.0 * h->n * S.off[S.nseg] * m;
+  h->stats.update_bytes += 8.0 * h->n * (S.off[S.nseg] + m + (beta != 0.0 ? m : 0));
   if (gemm_mode(h)) {
     const int sl = std::max(slices(h), min_slices);
     h->stats.update_tensor_flops += 2.0 * h->n * S.off[S.nseg] * m * sl * (sl + 1) / 2;
@@ -325,6 +328,7 @@ int to_host(lobpcg_ctx* h, double* dst, const double* src, int64_t count) {
   if (count <= 0) return LOBPCG_OK;
   LOB_CUDA_OK(cudaMemcpyAsync(h->hbuf, src, count * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   LOB_CUDA_OK(cudaStreamSynchronize(h->st));
+  ++h->syncs;
   memcpy(dst, h->hbuf, count * sizeof(double));
   h->timer.flush();
   return LOBPCG_OK;
@@ -459,6 +463,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   const auto t_start = std::chrono::steady_clock::now();
   const int64_t launches0 = g_launches;
   const int64_t eig0 = h->dense.eig_calls, eigf0 = h->dense.eig_fallbacks;
+  const int64_t syncs0 = h->syncs + h->dense.syncs;
   h->timer.st = h->st;
   h->timer.reset();
   h->timer.mark();
@@ -466,6 +471,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.n_x = nx;
   h->stats.flip_iteration = -1;
   h->stats.slice_escalation_iteration = -1;
+  h->stats.orth_error = -1.0;
   const int64_t ld = h->ld;
   const int s = h->opt.omega_rows > 0 ? h->opt.omega_rows : 16;
   const int maxit = h->opt.maxit > 0 ? h->opt.maxit : 2000;
@@ -729,6 +735,22 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
     if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
     if ((rc = residual_step(0, false))) return rc;
   }
+  // ---- ||X^T B X - I||_F of the returned columns from explicit FP64 products
+  {
+    const double* bx = h->X;
+    if (h->b_kind) {
+      if ((rc = apply_B(h, h->X, (int)k, h->BW))) return rc;
+      bx = h->BW;
+    }
+    if ((rc = gram_f64(h->st, n, seg1(h->X, ld, (int)k), seg1(bx, ld, (int)k), h->Gs, k, h->gwork,
+                       h->gwork_bytes)))
+      return rc;
+    double st3[3];
+    if ((rc = small_stats(h->dense, h->Gs, (int)k, (int)k, (int)k, true, h->colA, 0, h->colA, 0,
+                          st3)))
+      return rc;
+    h->stats.orth_error = st3[0];
+  }
   // ---- outputs
   if ((rc = sign_normalise(h->st, n, (int)k, h->X, ld, nullptr))) return rc;
   const cudaMemcpyKind kind =
@@ -749,6 +771,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.gpu_launches = g_launches - launches0;
   h->stats.eig_calls = h->dense.eig_calls - eig0;
   h->stats.eig_fallbacks = h->dense.eig_fallbacks - eigf0;
+  h->stats.host_syncs = h->syncs + h->dense.syncs - syncs0;
   h->stats.ms_spmm = h->timer.total[PH_SPMM];
   h->stats.ms_gram = h->timer.total[PH_GRAM];
   h->stats.ms_update = h->timer.total[PH_UPDATE];
