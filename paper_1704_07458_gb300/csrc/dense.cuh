@@ -27,6 +27,7 @@ struct DenseLayer {
   double* scal = nullptr;  // 16 device scalars
   double* host = nullptr;  // pinned host mirror, nmax + 64 doubles
   int64_t launches = 0;
+  int64_t syncs = 0;  // host waits on the stream
   // symmetric eigensolver (dense.cu): 0 = cuSOLVER FP64 syevd, 1 = FP32
   // cuSOLVER syevd refined to FP64 (Ogita-Aishima steps, Newton-Schulz,
   // cluster Jacobi, residual check with FP64 fallback)
