@@ -77,9 +77,15 @@ typedef struct {
   double tau_ortho;       /* 0: 100 eps; Algorithm 5 orthogonality tolerance */
   double tau_skip;        /* 0: 100 eps; switch to orthogonalisation when cond(R)^-3 < tau_skip (Sec. 5.3) */
   double max_seconds;     /* 0: no limit; host wall-clock limit -> LOBPCG_ERR_TIMEOUT */
-  int32_t dense_eig;      /* eigensolver of the projected matrices: 0 FP64 syevd (cuSOLVER);
-                             1 FP32 syevd refined to FP64 (Ogita-Aishima steps, Newton-Schulz,
-                             cluster Jacobi; FP64 syevd when its residual check fails) */
+  int32_t dense_eig;      /* small dense layer of the projected pencils (Algorithms 2, 4, 6, 7):
+                             0 this library's device-resident kernels for pencils of order
+                             <= 256 (FP32 eigendecomposition refined to FP64 on the device,
+                             Cholesky of the W-block Schur complement, FP32 Householder QR
+                             for C_p restored to FP64 orthonormality), cuSOLVER/cuBLAS FP64
+                             above that order and when the eigensolver's check fails;
+                             1 FP32 cuSOLVER syevd refined to FP64 (Ogita-Aishima steps,
+                             Newton-Schulz, cluster Jacobi; FP64 syevd when its residual
+                             check fails); 2 cuSOLVER FP64 syevd and cuBLAS throughout */
 } lobpcg_options_t;
 
 /* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
@@ -110,8 +116,9 @@ typedef struct {
   /* BF16 tensor-core work of the emulated contractions: the FP64-equivalent
    * flops times the S(S+1)/2 digit pairs of an S-slice split (0 in FP64 mode) */
   double gram_tensor_flops, update_tensor_flops;
-  /* projected eigenproblems solved by the refined FP32 eigensolver
-   * (dense_eig 1), and how many of them fell back to the FP64 syevd */
+  /* projected eigenproblems solved by this library's own eigensolvers (the
+   * device-resident one of dense_eig 0, or the refined FP32 one of
+   * dense_eig 1), and how many of them fell back to cuSOLVER's FP64 syevd */
   int64_t eig_calls, eig_fallbacks;
   /* emulated forms: iteration at which a stall (no column converging and the
    * leading backward error flat over 400 iterations) raised the contractions
@@ -283,10 +290,16 @@ int lobpcg_eig_adjoint(lobpcg_t h, int64_t k, const double* lambda, const double
  * A n x n column-major (leading dimension lda, device), symmetric (both
  * triangles read; it is symmetrised first).  On return A holds the
  * orthonormal eigenvectors and w (device, n) the eigenvalues ascending.
- * mode 0: cuSOLVER FP64 syevd; mode 1: FP32 decomposition refined to FP64
- * (Ogita-Aishima steps, a Newton-Schulz orthonormalisation, Jacobi on
- * eigenvalue clusters; FP64 syevd when its residual check fails).  n <= 8192.
- * Allocates its workspace per call and synchronises `stream`. */
+ * mode 0: cuSOLVER FP64 syevd; mode 1: FP32 cuSOLVER decomposition refined
+ * to FP64 (Ogita-Aishima steps, a Newton-Schulz orthonormalisation, Jacobi on
+ * eigenvalue clusters; FP64 syevd when its residual check fails); mode 2:
+ * this library's device-resident eigensolver (FP32 Householder
+ * tridiagonalisation, bisection and inverse iteration, then FP64
+ * Ogita-Aishima refinement, a Newton-Schulz step and Jacobi on clusters,
+ * n <= 256), cuSOLVER FP64 syevd when its check fails; mode 3: mode 2
+ * without the fallback, returning LOBPCG_ERR_NOT_CONVERGED (outputs written)
+ * when the check fails.  n <= 8192.  Allocates its workspace per call and
+ * synchronises `stream`. */
 int lobpcg_syev(int64_t n, double* A, int64_t lda, double* w, int mode, void* stream);
 
 /* Philox4x32-10 normals: Y(r, c) = normal number r*m + c of stream `stream_id`

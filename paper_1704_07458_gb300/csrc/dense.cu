@@ -714,10 +714,11 @@ int DenseLayer::init(cudaStream_t stream, int64_t n_max) {
   lwork = best;
   if (cudaMalloc(&work, (size_t)std::max(lwork, 1) * sizeof(double)) != cudaSuccess)
     return LOBPCG_ERR_OOM;
-  return LOBPCG_OK;
+  return dev.init(std::min<int64_t>(nmax, kDevDenseMax));
 }
 
 void DenseLayer::release() {
+  dev.release();
   for (auto& a : A) {
     if (a) cudaFree(a);
     a = nullptr;
@@ -753,6 +754,7 @@ void DenseLayer::release() {
 
 int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double* C,
                double* theta, bool* breakdown) {
+  if (dev_rr_fits(L, nx, nx, nx)) return rr_initial_dev(L, GA, GB, nx, C, theta, breakdown);
   *breakdown = false;
   double* MB = L.A[0];
   double* MA = L.A[1];
@@ -791,9 +793,12 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
   return LOBPCG_OK;
 }
 
-int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int nc,
-                bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
+int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
+                int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
                 int* npn_out, double* theta, double* PAP) {
+  if (dev_rr_fits(L, ns, nx, use_ortho ? 0 : ns - nx - np))
+    return rr_modified_dev(L, SAS, SBS, ns, nx, np, nc, use_ortho, tau_skip, flip, condR, C,
+                           npn_out, theta, PAP);
   *flip = false;
   *condR = 1.0;
   const int ld = ns;
@@ -891,6 +896,7 @@ int svqb_transform(DenseLayer& L, const double* G, int nu, bool drop, double tau
                    int* nkeep) {
   *nkeep = 0;
   if (nu <= 0) return LOBPCG_OK;
+  if (dev_rr_fits(L, nu, 0, 0)) return svqb_transform_dev(L, G, nu, drop, tau, T, nkeep);
   double* Z = L.A[0];
   int rc;
   if ((rc = dscale(L, nu, G, nu, Z, nu))) return rc;
@@ -942,10 +948,37 @@ int small_stats(DenseLayer& L, const double* G, int rows, int cols, int ldg, boo
 // Kernel-level entry point of the projected eigensolver (see lobpcg.h).
 LOBPCG_EXPORT int lobpcg_syev(int64_t n, double* A, int64_t lda, double* w, int mode,
                               void* stream) {
-  if (n <= 0 || n > 8192 || lda < n || !A || !w || (mode != 0 && mode != 1))
+  if (n <= 0 || n > 8192 || lda < n || !A || !w || mode < 0 || mode > 3 ||
+      (mode >= 2 && n > lob::kDevDenseMax))
     return LOBPCG_ERR_ARG;
   lob::DenseLayer L;
   int rc = L.init((cudaStream_t)stream, n);
+  bool unchecked = false;
+  if (!rc && mode >= 2) {
+    // the device-resident eigensolver, cuSOLVER FP64 when its check fails
+    double* M = L.A[0];
+    double* Z = L.A[1];
+    int* status = L.dev.ints + 2;
+    rc = lob::copy_mat(L, (int)n, (int)n, A, (int)lda, M, (int)n);
+    if (!rc) rc = lob::dev_syev(L, (int)n, M, (int)n, Z, (int)n, L.ev, status);
+    int st = 0;
+    if (!rc && (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, L.st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(L.st) != cudaSuccess))
+      rc = LOBPCG_ERR_CUDA;
+    if (!rc && st != 0 && mode == 2) {
+      rc = lob::copy_mat(L, (int)n, (int)n, M, (int)n, Z, (int)n);
+      if (!rc) rc = lob::syevd_fallback(L, (int)n, Z, (int)n);
+    }
+    unchecked = !rc && st != 0 && mode == 3;
+    if (!rc) rc = lob::copy_mat(L, (int)n, (int)n, Z, (int)n, A, (int)lda);
+    if (!rc && cudaMemcpyAsync(w, L.ev, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st) !=
+                   cudaSuccess)
+      rc = LOBPCG_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(L.st) != cudaSuccess) rc = LOBPCG_ERR_CUDA;
+    L.release();
+    return unchecked ? LOBPCG_ERR_NOT_CONVERGED : rc;
+  }
   if (!rc) {
     L.eig_mode = mode;
     double* M = L.A[0];

@@ -8,9 +8,32 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace lob {
+
+// Device-resident path (dense_dev.cu): projected pencils of order <= 256.
+constexpr int kDevDenseMax = 256;
+
+struct DevDense {
+  int nmax = 0;
+  std::vector<void*> bufs;
+  double *X = nullptr, *X1 = nullptr, *E = nullptr, *Zt = nullptr;  // nmax x nmax
+  double *T1 = nullptr, *T2 = nullptr, *T3 = nullptr, *T4 = nullptr;
+  double *XA = nullptr, *GS = nullptr;  // nmax x 2 nmax: [X | A X], [G | S]
+  float *V32 = nullptr, *Y32 = nullptr;  // nmax x nmax FP32
+  float* f32v = nullptr;                 // 4 nmax FP32 vectors
+  double* vec = nullptr;                 // 8 nmax
+  double* scal = nullptr;                // 16 device scalars
+  int* ints = nullptr;                   // flags, permutation, cluster runs
+  double* part = nullptr;                // GEMM split-K partial tiles
+  unsigned* cnt = nullptr;               // GEMM split-K tile counters (zero between launches)
+  int cnt_tiles = 0;
+  int init(int64_t n_max);
+  void release();
+};
 
 struct DenseLayer {
   cudaStream_t st = nullptr;
@@ -28,10 +51,14 @@ struct DenseLayer {
   double* host = nullptr;  // pinned host mirror, nmax + 64 doubles
   int64_t launches = 0;
   int64_t syncs = 0;  // host waits on the stream
-  // symmetric eigensolver (dense.cu): 0 = cuSOLVER FP64 syevd, 1 = FP32
-  // cuSOLVER syevd refined to FP64 (Ogita-Aishima steps, Newton-Schulz,
-  // cluster Jacobi, residual check with FP64 fallback)
+  // projected eigenproblems: 0 = the device-resident layer of dense_dev.cu
+  // for orders <= kDevDenseMax (cuSOLVER FP64 syevd above, and as the
+  // fallback when its residual check fails), 1 = FP32 cuSOLVER syevd refined
+  // to FP64 (Ogita-Aishima steps, Newton-Schulz, cluster Jacobi, residual
+  // check with FP64 fallback), 2 = cuSOLVER FP64 syevd throughout
   int eig_mode = 0;
+  int64_t dev_calls = 0, dev_fallbacks = 0;  // device-path eigensolves and their fallbacks
+  DevDense dev;
   int64_t eig_calls = 0, eig_fallbacks = 0;
   double* R[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // refinement blocks
   float *Af = nullptr, *wf = nullptr, *swork = nullptr;
@@ -54,8 +81,10 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
 // writes C = [C_x, C_p] (ns x (nx + *npn), leading dim ns), theta (device, nx)
 // and PAP (npn x npn, leading dim npn).  *flip reports the switch to the
 // orthogonal branch (Cholesky failure or cond(R)^-3 < tau_skip).
-int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int nc,
-                bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
+// np: columns of P in S = [X, P, W] (the identities (12)-(13) make S^T B S
+// the identity outside the W columns, which the device path uses).
+int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
+                int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
                 int* npn, double* theta, double* PAP);
 
 // svqb (drop == false, Algorithm 4) or svqbDrop (drop == true, Algorithm 6) on
@@ -75,5 +104,27 @@ int assemble(DenseLayer& L, int nx, int np, int nw, const double* theta, const d
 // out[2] = sum(b[0:nb]).  G: rows x cols, leading dim ldg.  Result to host.
 int small_stats(DenseLayer& L, const double* G, int rows, int cols, int ldg, bool identity,
                 const double* a, int na, const double* b, int nb, double out[3]);
+
+// ---- device-resident path (dense_dev.cu)
+// C = alpha op(A) op(B) + beta Cin, column-major, m, n <= 2 * the layer's
+// order; skip: device flag, the launch is a no-op when it is non-zero.
+int dev_gemm(DenseLayer& L, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+             int lda, const double* B, int ldb, double beta, const double* Cin, int ldcin,
+             double* C, int ldc, const int* skip);
+int dev_chol(DenseLayer& L, int n, double* A, int lda, int* info);
+int dev_trinv(DenseLayer& L, int n, const double* R, int ldr, double* X, int ldx, const int* skip);
+int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz, double* w,
+             int* status);
+int dev_orth_basis(DenseLayer& L, int m, int c, const double* M, int ldm, double* Q, int ldq);
+bool dev_rr_fits(const DenseLayer& L, int ns, int nx, int nw);
+int rr_initial_dev(DenseLayer& L, const double* GA, const double* GB, int nx, double* C,
+                   double* theta, bool* breakdown);
+int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
+                    int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
+                    int* npn, double* theta, double* PAP);
+int svqb_transform_dev(DenseLayer& L, const double* G, int nu, bool drop, double tau, double* T,
+                       int* nkeep);
+// cuSOLVER FP64 eigendecomposition in place (A: eigenvectors, L.ev: eigenvalues)
+int syevd_fallback(DenseLayer& L, int n, double* A, int lda);
 
 }  // namespace lob

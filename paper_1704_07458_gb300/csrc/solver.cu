@@ -242,7 +242,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   const int64_t rb = std::max(residual_workspace(n, (int)h->ld), colsumsq_workspace(n, (int)h->ld));
   if ((rc = dalloc(h, &h->rwork, (size_t)rb))) return rc;
   if ((rc = h->dense.init(h->st, nsmax))) return rc;
-  h->dense.eig_mode = h->opt.dense_eig == 1 ? 1 : 0;  // 0 FP64 syevd, 1 refined FP32
+  h->dense.eig_mode = (h->opt.dense_eig == 1 || h->opt.dense_eig == 2) ? h->opt.dense_eig : 0;
   h->ws_n = n;
   h->ws_nx = nx;
   h->ws_b = h->b_kind;
@@ -462,7 +462,8 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   if (rc) return h->fail(rc, "workspace allocation failed");
   const auto t_start = std::chrono::steady_clock::now();
   const int64_t launches0 = g_launches;
-  const int64_t eig0 = h->dense.eig_calls, eigf0 = h->dense.eig_fallbacks;
+  const int64_t eig0 = h->dense.eig_calls + h->dense.dev_calls,
+                eigf0 = h->dense.eig_fallbacks + h->dense.dev_fallbacks;
   const int64_t syncs0 = h->syncs + h->dense.syncs;
   h->timer.st = h->st;
   h->timer.reset();
@@ -627,7 +628,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       int npn = 0;
       {
         Scoped sd(h->timer, PH_DENSE);
-        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, (int)nc, use_ortho, tau_skip,
+        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, np, (int)nc, use_ortho, tau_skip,
                               &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
           return rc;
       }
@@ -639,7 +640,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
         if ((rc = project(true, h->SAS, h->SBS))) return rc;
         ns = (int)nx + np + nw;
         Scoped sd(h->timer, PH_DENSE);
-        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, (int)nc, true, tau_skip,
+        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, np, (int)nc, true, tau_skip,
                               &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
           return rc;
       }
@@ -769,8 +770,8 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.iterations = it;
   h->stats.converged = nc;
   h->stats.gpu_launches = g_launches - launches0;
-  h->stats.eig_calls = h->dense.eig_calls - eig0;
-  h->stats.eig_fallbacks = h->dense.eig_fallbacks - eigf0;
+  h->stats.eig_calls = h->dense.eig_calls + h->dense.dev_calls - eig0;
+  h->stats.eig_fallbacks = h->dense.eig_fallbacks + h->dense.dev_fallbacks - eigf0;
   h->stats.host_syncs = h->syncs + h->dense.syncs - syncs0;
   h->stats.ms_spmm = h->timer.total[PH_SPMM];
   h->stats.ms_gram = h->timer.total[PH_GRAM];

@@ -5,6 +5,9 @@ clustered to 1e-9, exactly degenerate), and the 18 x 18 and 54 x 54 projected
 pencils that the oracle's Algorithm 7 builds on the 16^3 generalised pencil.
 The bar is that of an FP64 eigensolver: eigenvalues within 1e-13 ||A||,
 orthonormality and residual ||A Z - Z diag(w)|| within 1e-13 ||A||.
+Modes: 0 cuSOLVER FP64, 1 FP32 cuSOLVER refined, 2 the device-resident
+eigensolver with its fallback, 3 the device-resident eigensolver alone (its
+own check must pass on every case).
 """
 import numpy as np
 import pytest
@@ -35,6 +38,14 @@ def _cases():
     out.append(("clusters", _spectrum_matrix(71, np.sort(w), 3)))
     w = np.sort(np.concatenate([rng.uniform(1e-14, 1e-12, 5), rng.uniform(0.1, 50, 45)]))
     out.append(("tiny eigenvalues", _spectrum_matrix(50, w, 4)))
+    # the spectrum of a Rayleigh-Ritz matrix of the 64^3 pencil: 71 Ritz
+    # values in [0.007, 0.08] (one pair 1e-6 apart, one triple 3e-7 apart,
+    # below FP32 resolution at this norm) and 142 values in [0.1, 12]
+    low = np.sort(rng.uniform(0.007, 0.08, 71))
+    low[20] = low[19] + 1e-6
+    low[40:43] = low[40] + np.array([0.0, 3e-7, 9e-7])
+    w = np.sort(np.concatenate([low, rng.uniform(0.1, 12, 142)]))
+    out.append(("ritz-like", _spectrum_matrix(213, w, 5)))
     return out
 
 
@@ -66,12 +77,12 @@ def _run(A, mode):
     At = torch.from_numpy(np.asfortranarray(A).ravel(order="F").copy()).cuda()
     w = torch.empty(n, dtype=torch.float64, device="cuda")
     rc = gb.lobpcg_syev(n, At, n, w, mode)
-    assert rc == 0
+    assert rc == 0, rc
     Z = At.cpu().numpy().reshape(n, n, order="F")
     return w.cpu().numpy(), Z
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_syev_matches_lapack(mode):
     for name, A in _cases() + _projected():
         A = 0.5 * (A + A.T)
