@@ -480,6 +480,8 @@ def main():
                    "ortho_calls": int(st["ortho_calls"]), "svqb_passes": int(st["svqb_passes"]),
                    "dropped_columns": int(st["dropped_columns"]),
                    "eig_calls": int(st["eig_calls"]), "eig_fallbacks": int(st["eig_fallbacks"]),
+                   "eig_check_failures": {k: int(st[f"eig_check_{k}"]) for k in
+                                          ("orthogonality", "wide_cluster", "nonfinite")},
                    "slice_escalation_iteration": int(st["slice_escalation_iteration"]),
                    "host_syncs_per_solve": int(tot["host_syncs"]) // max(1, args.steps),
                    "launches_per_solve": int(tot["gpu_launches"]) // max(1, args.steps)},

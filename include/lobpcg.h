@@ -133,6 +133,11 @@ typedef struct {
   double orth_error;
   /* host waits on the stream (device scalars read back) during the solve */
   int64_t host_syncs;
+  /* why the device-resident eigensolver (dense_eig 0) fell back: its
+   * refined eigenvectors failed the orthonormality check, a group of
+   * coupled eigenvalues was wider than its cluster Jacobi takes (32), or a
+   * value was not finite (a call may count under several) */
+  int64_t eig_check_orthogonality, eig_check_wide_cluster, eig_check_nonfinite;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.

@@ -90,6 +90,9 @@ class lobpcg_stats_t(ctypes.Structure):
         ("update_bytes", ctypes.c_double),
         ("orth_error", ctypes.c_double),
         ("host_syncs", ctypes.c_int64),
+        ("eig_check_orthogonality", ctypes.c_int64),
+        ("eig_check_wide_cluster", ctypes.c_int64),
+        ("eig_check_nonfinite", ctypes.c_int64),
     ]
 
     def as_dict(self):

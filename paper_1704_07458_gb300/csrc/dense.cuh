@@ -58,6 +58,7 @@ struct DenseLayer {
   // check with FP64 fallback), 2 = cuSOLVER FP64 syevd throughout
   int eig_mode = 0;
   int64_t dev_calls = 0, dev_fallbacks = 0;  // device-path eigensolves and their fallbacks
+  int64_t check_fail[3] = {0, 0, 0};         // failed checks: orthogonality, wide run, non-finite
   DevDense dev;
   int64_t eig_calls = 0, eig_fallbacks = 0;
   double* R[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // refinement blocks

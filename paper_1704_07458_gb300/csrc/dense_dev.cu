@@ -121,37 +121,39 @@ constexpr int kCholMax = 160;
 __global__ void __launch_bounds__(256) chol64_kernel(int n, double* A, int lda, int* info) {
   extern __shared__ double sa[];  // n x n, column-major, leading dimension n
   __shared__ int s_fail;
-  const int t = threadIdx.x;
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    sa[e] = r <= c ? A[r + (int64_t)c * lda] : 0.0;
-  }
+  __shared__ double s_r, s_inv;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (int)blockDim.x >> 5;
+  for (int c = warp; c < n; c += nw)
+    for (int r = lane; r < n; r += 32) sa[r + c * n] = r <= c ? A[r + (int64_t)c * lda] : 0.0;
   if (t == 0) s_fail = 0;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    const double piv = sa[j + j * n];
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (t == 0) s_fail = j + 1;
-      break;
+    if (t == 0) {  // one square root and one division per step
+      const double piv = sa[j + j * n];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        s_fail = j + 1;
+      } else {
+        s_r = sqrt(piv);
+        s_inv = 1.0 / s_r;
+      }
     }
-    const double rjj = sqrt(piv);
     __syncthreads();
+    if (s_fail) break;
+    const double rjj = s_r, inv = s_inv;
     // row j of R: r_jk = a_jk / r_jj (k >= j)
-    for (int c = j + t; c < n; c += blockDim.x) sa[j + c * n] = c == j ? rjj : sa[j + c * n] / rjj;
+    for (int c = j + t; c < n; c += blockDim.x) sa[j + c * n] = c == j ? rjj : sa[j + c * n] * inv;
     __syncthreads();
-    // trailing update of the upper triangle: a_ik -= r_ji r_jk, j < i <= k
-    const int m = n - j - 1;
-    for (int e = t; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e % m, c = j + 1 + e / m;
-      if (i <= c) sa[i + c * n] = fma(-sa[j + i * n], sa[j + c * n], sa[i + c * n]);
+    // trailing update of the upper triangle: a_ic -= r_ji r_jc, j < i <= c
+    // (a warp per column c, lanes over rows i)
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      const double rjc = sa[j + c * n];
+      for (int i = j + 1 + lane; i <= c; i += 32) sa[i + c * n] = fma(-sa[j + i * n], rjc, sa[i + c * n]);
     }
     __syncthreads();
   }
   __syncthreads();
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    A[r + (int64_t)c * lda] = r <= c ? sa[e] : 0.0;
-  }
+  for (int c = warp; c < n; c += nw)
+    for (int r = lane; r < n; r += 32) A[r + (int64_t)c * lda] = r <= c ? sa[r + c * n] : 0.0;
   if (t == 0) info[0] = s_fail;
 }
 
@@ -163,37 +165,36 @@ __global__ void __launch_bounds__(256) trinv64_kernel(int n, const double* R, in
                                                       int ldx, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ double sm[];  // n x n: R, rows turning into X from the bottom
-  const int t = threadIdx.x;
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int i = e % n, c = e / n;
-    sm[e] = i <= c ? R[i + (int64_t)c * ldr] : 0.0;
-  }
+  __shared__ double dinv[kCholMax];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwp = (int)blockDim.x >> 5;
+  for (int c = warp; c < n; c += nwp)
+    for (int i = lane; i < n; i += 32) sm[i + c * n] = i <= c ? R[i + (int64_t)c * ldr] : 0.0;
+  for (int i = t; i < n; i += blockDim.x) dinv[i] = 1.0 / R[i + (int64_t)i * ldr];
   __syncthreads();
+  // eight lanes per column c share its dot product (a shuffle reduction), so
+  // a row costs (n - i) / 8 dependent steps instead of n - i
+  const int sub = t & 7, grp = t >> 3, ngrp = (int)blockDim.x >> 3;
   for (int i = n - 1; i >= 0; --i) {
-    const double inv = 1.0 / sm[i + i * n];
-    double val[2] = {0.0, 0.0};
-    for (int h = 0; h < 2; ++h) {
-      const int c = i + t + h * (int)blockDim.x;
-      if (c >= n) continue;
-      if (c == i) {
-        val[h] = inv;
-      } else {
-        double s = 0.0;
-        for (int kk = i + 1; kk <= c; ++kk) s = fma(sm[i + kk * n], sm[kk + c * n], s);
-        val[h] = -s * inv;
+    const double inv = dinv[i];
+    double val[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int h = 0; h < 5; ++h) {
+      const int c = i + grp + h * ngrp;  // uniform within each group of 8 lanes
+      double sacc = 0.0;
+      if (c < n && c > i)
+        for (int kk = i + 1 + sub; kk <= c; kk += 8) sacc = fma(sm[i + kk * n], sm[kk + c * n], sacc);
+      for (int o = 4; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      val[h] = c == i ? inv : -sacc * inv;
+    }
+    __syncthreads();
+    if (sub == 0)
+      for (int h = 0; h < 5; ++h) {
+        const int c = i + grp + h * ngrp;
+        if (c < n) sm[i + c * n] = val[h];
       }
-    }
-    __syncthreads();
-    for (int h = 0; h < 2; ++h) {
-      const int c = i + t + h * (int)blockDim.x;
-      if (c < n) sm[i + c * n] = val[h];
-    }
     __syncthreads();
   }
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int i = e % n, c = e / n;
-    X[i + (int64_t)c * ldx] = sm[e];
-  }
+  for (int c = warp; c < n; c += nwp)
+    for (int i = lane; i < n; i += 32) X[i + (int64_t)c * ldx] = sm[i + c * n];
 }
 
 // ------------------------------------------- FP32 tridiagonalisation
@@ -305,6 +306,126 @@ __global__ void __launch_bounds__(1024, 1) tridiag32_kernel(int n, const double*
   }
 }
 
+// The same reduction with the lower triangle kept in a full n x ld array
+// (ld = n rounded up to odd, n <= kTridFull) in shared memory: the product
+// p = tau A22 v runs one thread per row (row i reads A(i, j), j <= i, along
+// its row and A(j, i), j > i, down its column; with an odd ld both patterns
+// are free of bank conflicts across a warp), four accumulators per thread;
+// the rank-2 update touches the lower triangle only.
+constexpr int kTridFull = 223;
+
+__global__ void __launch_bounds__(1024, 1) tridiag32_full_kernel(int n, const double* A, int lda,
+                                                                 float* d, float* e, float* V,
+                                                                 int ldv, float* tau,
+                                                                 double* scal) {
+  extern __shared__ float F[];  // n x ld, F[i * ld + j] = A(i, j) for j <= i
+  __shared__ float v[256], p[256];
+  __shared__ float wpart[32];
+  __shared__ float s_tau;
+  __shared__ double fro[32];
+  const int ld = n | 1;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double f = 0.0;
+  for (int i = warp; i < n; i += 32)
+    for (int j = lane; j <= i; j += 32) {
+      const double a = 0.5 * (A[i + (int64_t)j * lda] + A[j + (int64_t)i * lda]);
+      F[i * ld + j] = (float)a;
+      f += (i == j ? 1.0 : 2.0) * a * a;
+    }
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (lane == 0) fro[warp] = f;
+  __syncthreads();
+  if (t == 0) {
+    double sacc = 0.0;
+    for (int w = 0; w < 32; ++w) sacc += fro[w];
+    scal[0] = sqrt(sacc);
+  }
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const int o = k + 1;  // first row / column of the trailing block
+    if (warp == 0) {
+      // x = A(k+1 .. n-1, k): column k below the diagonal (stride ld)
+      float ss = 0.f;
+      for (int i = 1 + lane; i < m; i += 32) {
+        const float x = F[(o + i) * ld + k];
+        ss = fmaf(x, x, ss);
+      }
+      for (int q = 16; q > 0; q >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, q);
+      const float alpha = F[o * ld + k];
+      float tk = 0.f, beta = alpha, scale = 0.f;
+      if (ss > 0.f) {
+        beta = -copysignf(sqrtf(alpha * alpha + ss), alpha);
+        tk = (beta - alpha) / beta;
+        scale = 1.f / (alpha - beta);
+      }
+      for (int i = lane; i < m; i += 32) {
+        const float vi = i == 0 ? 1.f : (tk != 0.f ? F[(o + i) * ld + k] * scale : 0.f);
+        v[i] = vi;
+        V[(o + i) + (int64_t)k * ldv] = vi;
+      }
+      if (lane == 0) {
+        s_tau = tk;
+        d[k] = F[k * ld + k];
+        e[k] = beta;
+        tau[k] = tk;
+      }
+    }
+    __syncthreads();
+    const float tk = s_tau;
+    if (tk == 0.f) continue;
+    // p_i = tau sum_j A22(i, j) v_j, one thread per row
+    float pv = 0.f;
+    if (t < m) {
+      const int gi = o + t;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      const float* row = F + gi * ld + o;  // A(gi, o + j), j <= t
+      int j = 0;
+      for (; j + 3 <= t; j += 4) {
+        a0 = fmaf(row[j], v[j], a0);
+        a1 = fmaf(row[j + 1], v[j + 1], a1);
+        a2 = fmaf(row[j + 2], v[j + 2], a2);
+        a3 = fmaf(row[j + 3], v[j + 3], a3);
+      }
+      for (; j <= t; ++j) a0 = fmaf(row[j], v[j], a0);
+      const float* col = F + gi;  // A(o + j, gi) = F[(o + j) * ld + gi], j > t
+      for (j = t + 1; j + 3 < m; j += 4) {
+        a0 = fmaf(col[(o + j) * ld], v[j], a0);
+        a1 = fmaf(col[(o + j + 1) * ld], v[j + 1], a1);
+        a2 = fmaf(col[(o + j + 2) * ld], v[j + 2], a2);
+        a3 = fmaf(col[(o + j + 3) * ld], v[j + 3], a3);
+      }
+      for (; j < m; ++j) a0 = fmaf(col[(o + j) * ld], v[j], a0);
+      const float sacc = tk * ((a0 + a1) + (a2 + a3));
+      p[t] = sacc;
+      pv = sacc * v[t];
+    }
+    for (int q = 16; q > 0; q >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, q);
+    if (lane == 0) wpart[warp] = pv;
+    __syncthreads();
+    float ptv = 0.f;
+    for (int w = 0; w < 32; ++w) ptv += wpart[w];
+    const float K = 0.5f * tk * ptv;
+    // rank-2 update of the lower triangle: A22(i, j) -= v_i w_j + w_i v_j
+    for (int i = warp; i < m; i += 32) {
+      float* row = F + (o + i) * ld + o;
+      const float vi = v[i], wi = p[i] - K * v[i];
+      for (int j = lane; j <= i; j += 32) row[j] = row[j] - (vi * (p[j] - K * v[j]) + wi * v[j]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (n >= 2) {
+      d[n - 2] = F[(n - 2) * ld + (n - 2)];
+      d[n - 1] = F[(n - 1) * ld + (n - 1)];
+      e[n - 2] = F[(n - 1) * ld + (n - 2)];
+      tau[n - 2] = 0.f;
+    } else {
+      d[0] = F[0];
+    }
+    tau[n - 1] = 0.f;
+  }
+}
+
 // --------------------------- tridiagonal eigenvalues and eigenvectors
 // One thread per eigenvalue index j (32 per CTA): bisection on the Sturm
 // count for lambda_j (FP32), then two steps of inverse iteration with T -
@@ -324,9 +445,77 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   return (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;  // [-1, 1)
 }
 
+// lam[j], j = 0 .. n-1: the eigenvalues of T by multisection on the Sturm
+// count (count(x) = number of eigenvalues below x, LAPACK's pivmin guard),
+// four lanes per eigenvalue evaluating four interior points of the interval
+// at once (each round narrows it five-fold), to FP32 resolution.
+__global__ void __launch_bounds__(256) bisect_kernel(int n, const float* __restrict__ dg,
+                                                     const float* __restrict__ eg,
+                                                     float* __restrict__ lam) {
+  __shared__ float d[256], e2[256];
+  __shared__ float s_gl, s_gu, s_piv;
+  const int t = threadIdx.x;
+  for (int i = t; i < n; i += blockDim.x) {
+    d[i] = dg[i];
+    const float ei = i + 1 < n ? eg[i] : 0.f;
+    e2[i] = ei * ei;
+  }
+  __syncthreads();
+  if (t == 0) {
+    float gl = FLT_MAX, gu = -FLT_MAX, emax2 = 0.f;
+    for (int i = 0; i < n; ++i) {
+      const float r = (i > 0 ? sqrtf(e2[i - 1]) : 0.f) + (i + 1 < n ? sqrtf(e2[i]) : 0.f);
+      gl = fminf(gl, d[i] - r);
+      gu = fmaxf(gu, d[i] + r);
+      emax2 = fmaxf(emax2, e2[i]);
+    }
+    const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
+    const float pivmin = FLT_MIN * fmaxf(1.f, emax2);
+    s_gl = gl - 2.f * FLT_EPSILON * tnorm * n - pivmin;
+    s_gu = gu + 2.f * FLT_EPSILON * tnorm * n + pivmin;
+    s_piv = pivmin;
+  }
+  __syncthreads();
+  const int g = (blockIdx.x * blockDim.x + t) >> 2, q = t & 3;
+  const bool active = g < n;
+  const float pivmin = s_piv;
+  float lo = s_gl, hi = s_gu;
+  for (int round = 0; round < 24; ++round) {
+    const float wdt = hi - lo;
+    const bool conv = !(wdt > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin);
+    // the four lanes of a group share lo, hi: they stop together
+    const float x = lo + (float)(q + 1) * 0.2f * wdt;
+    int c = 0;
+    if (active && !conv) {
+      float qq = 1.f;
+      for (int i = 0; i < n; ++i) {
+        qq = d[i] - x - (i > 0 ? e2[i - 1] / qq : 0.f);
+        if (fabsf(qq) < pivmin) qq = -pivmin;
+        c += qq < 0.f;
+      }
+    }
+    // first of the four points with count > g: the eigenvalue lies below it
+    const unsigned above = __ballot_sync(0xffffffffu, active && !conv && c > g);
+    const unsigned grp = (above >> ((t & 31) & ~3)) & 0xFu;
+    const int first = grp ? __ffs(grp) - 1 : 4;
+    const float x0 = lo + (float)first * 0.2f * wdt, x1 = lo + (float)(first + 1) * 0.2f * wdt;
+    if (!conv) {
+      lo = first == 0 ? lo : x0;
+      hi = first == 4 ? hi : x1;
+    }
+  }
+  if (active && q == 0) lam[g] = 0.5f * (lo + hi);
+}
+
+// Inverse iteration (two steps) for eigenvalue lam[j] of T, one thread per j
+// (32 per CTA), with T - lam_j I factored by Gaussian elimination with
+// partial pivoting (the method of LAPACK's stein), from a start vector hashed
+// from j so that members of a tight cluster start in different directions.
+// Per-thread work arrays live in shared memory interleaved by lane.  Y(:, j)
+// (FP32, n x n column-major) receives the unit eigenvector of T.
 __global__ void __launch_bounds__(32) tridiag_eig_kernel(int n, const float* __restrict__ dg,
                                                          const float* __restrict__ eg,
-                                                         float* __restrict__ lam,
+                                                         const float* __restrict__ lam,
                                                          float* __restrict__ Y, int ldy) {
   extern __shared__ float ws[];  // d, e, e^2 (3 n) then 6 arrays of n x 32
   float* d = ws;
@@ -355,27 +544,9 @@ __global__ void __launch_bounds__(32) tridiag_eig_kernel(int n, const float* __r
   }
   const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
   const float pivmin = FLT_MIN * fmaxf(1.f, emax2);
-  gl -= 2.f * FLT_EPSILON * tnorm * n + pivmin;
-  gu += 2.f * FLT_EPSILON * tnorm * n + pivmin;
   const int j = blockIdx.x * 32 + lane;
   if (j >= n) return;
-  // ---- bisection: count(x) = number of eigenvalues < x
-  float lo = gl, hi = gu;
-  for (int it = 0; it < 64; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (!(mid > lo && mid < hi)) break;
-    if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
-    int c = 0;
-    float q = 1.f;
-    for (int i = 0; i < n; ++i) {
-      q = d[i] - mid - (i > 0 ? e2[i - 1] / q : 0.f);
-      if (fabsf(q) < pivmin) q = -pivmin;
-      c += q < 0.f;
-    }
-    if (c > j) hi = mid; else lo = mid;
-  }
-  const float L = 0.5f * (lo + hi);
-  lam[j] = L;
+  const float L = lam[j];
   // ---- LU with partial pivoting of T - L I (rows i, i + 1 may swap):
   // U has diagonal u0, superdiagonals u1, u2; multipliers in lm, swaps in sw
   const float pert = FLT_EPSILON * tnorm + pivmin;
@@ -494,31 +665,45 @@ __global__ void __launch_bounds__(1024, 1) cluster_orth_kernel(int n, const floa
 
 // Z = Q Y with Q = H_0 H_1 ... H_{n-3}, H_k = I - tau_k v_k v_k^T: reflectors
 // applied from the last to the first, each column of Y independently (one
-// half-warp per column, 16 columns per CTA).  Z is written in FP64.
+// half-warp per column, 16 columns per CTA).  The reflectors are staged in
+// shared memory (packed, strictly lower part) so that the n sequential
+// reflector steps read no global memory.  Z is written in FP64.
+__device__ __forceinline__ int vpk(int n, int k) {  // start of reflector k (rows k+1 .. n-1)
+  return k * (n - 1) - (k * (k - 1)) / 2;
+}
+
 __global__ void __launch_bounds__(256) backtransform_kernel(int n, const float* __restrict__ V,
                                                             int ldv, const float* __restrict__ tau,
                                                             const float* __restrict__ Y, int ldy,
                                                             double* __restrict__ Z, int ldz) {
-  extern __shared__ float ys[];  // n x 16
+  extern __shared__ float bs[];
+  float* vp = bs;                          // n (n - 1) / 2
+  float* ys = bs + (n * (n - 1)) / 2;      // 16 x n
+  __shared__ float ts[256];
   const int t = threadIdx.x, c = t >> 4, r = t & 15;
+  for (int k = 0; k + 1 < n; ++k) {
+    const int base = vpk(n, k), len = n - 1 - k;
+    for (int i = t; i < len; i += blockDim.x) vp[base + i] = V[(k + 1 + i) + (int64_t)k * ldv];
+  }
+  for (int k = t; k < n; k += blockDim.x) ts[k] = tau[k];
   const int col = blockIdx.x * 16 + c;
   const bool active = col < n;
   float* y = ys + c * n;
   if (active)
     for (int i = r; i < n; i += 16) y[i] = Y[i + (int64_t)col * ldy];
-  __syncwarp();
+  __syncthreads();
   const unsigned mask = 0xFFFFu << (16 * ((t >> 4) & 1));
   for (int k = n - 3; k >= 0; --k) {
-    const float tk = __ldg(tau + k);
+    const float tk = ts[k];
     if (tk == 0.f) continue;
-    const float* v = V + (int64_t)k * ldv;
-    float s = 0.f;
+    const float* v = vp + vpk(n, k) - (k + 1);  // v[i] for i = k+1 .. n-1
+    float sacc = 0.f;
     if (active)
-      for (int i = k + 1 + r; i < n; i += 16) s = fmaf(__ldg(v + i), y[i], s);
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(mask, s, o);
-    s *= tk;
+      for (int i = k + 1 + r; i < n; i += 16) sacc = fmaf(v[i], y[i], sacc);
+    for (int o = 8; o > 0; o >>= 1) sacc += __shfl_xor_sync(mask, sacc, o);
+    sacc *= tk;
     if (active)
-      for (int i = k + 1 + r; i < n; i += 16) y[i] = fmaf(-s, __ldg(v + i), y[i]);
+      for (int i = k + 1 + r; i < n; i += 16) y[i] = fmaf(-sacc, v[i], y[i]);
     __syncwarp(mask);
   }
   if (active)
@@ -532,28 +717,29 @@ __global__ void __launch_bounds__(256) backtransform_kernel(int n, const float* 
 // quotient is below 1e-2 (a first-order correction), else r_ij / 2 (the pair
 // is treated as a cluster: orthogonalised only); E_ii = r_ii / 2.  Sets
 // done[0] when delta <= 64 n eps ||A||_F (converged: later steps skip).
-// One CTA.
-__global__ void __launch_bounds__(1024, 1) oa_step_kernel(int n, const double* __restrict__ GS,
-                                                          const double* __restrict__ scal,
-                                                          double* __restrict__ E, int* done,
-                                                          double* delta_out) {
+// Two kernels over the whole GPU: partial norms and d, then delta and E.
+constexpr int kOaBlocks = 64;
+
+__global__ void __launch_bounds__(256) oa_norms_kernel(int n, const double* __restrict__ GS,
+                                                       double* __restrict__ part,
+                                                       double* __restrict__ dvec, const int* done) {
   if (*done) return;
-  __shared__ double red[2][32];
-  __shared__ double s_delta;
+  __shared__ double red[2][8];
   const double* G = GS;
   const double* S = GS + (int64_t)n * n;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double a = 0.0, b = 0.0;
-  const int nn = n * n;
-  for (int e = t; e < nn; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    const double g = G[e], s = S[e];
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + t; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const double g = G[e], sv = S[e];
     if (i == j) {
-      const double dd = s / g;
-      a = fma(s - dd * g, s - dd * g, a);
+      const double dd = sv / g;
+      dvec[i] = dd;
+      a = fma(sv - dd * g, sv - dd * g, a);
       b = fma(1.0 - g, 1.0 - g, b);
     } else {
-      a = fma(s, s, a);
+      a = fma(sv, sv, a);
       b = fma(g, g, b);
     }
   }
@@ -568,31 +754,56 @@ __global__ void __launch_bounds__(1024, 1) oa_step_kernel(int n, const double* _
   __syncthreads();
   if (t == 0) {
     double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < 32; ++w) {
+    for (int w = 0; w < 8; ++w) {
       sa += red[0][w];
       sb += red[1][w];
     }
-    const double normA = scal[0];
-    const double delta = 2.0 * (sqrt(sa) + normA * sqrt(sb));
-    s_delta = delta;
-    delta_out[0] = delta;
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sb;
+  }
+}
+
+__global__ void __launch_bounds__(256) oa_e_kernel(int n, const double* __restrict__ GS,
+                                                   const double* __restrict__ part,
+                                                   const double* __restrict__ dvec,
+                                                   const double* __restrict__ scal,
+                                                   double* __restrict__ E, int* done,
+                                                   double* delta_out) {
+  if (*done) return;
+  __shared__ double s_delta;
+  const double* G = GS;
+  const double* S = GS + (int64_t)n * n;
+  if (threadIdx.x < 32) {  // fixed-order sum of the partials (every CTA alike)
+    double sa = 0.0, sb = 0.0;
+    for (int q = threadIdx.x; q < kOaBlocks; q += 32) {
+      sa += part[2 * q];
+      sb += part[2 * q + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (threadIdx.x == 0) s_delta = 2.0 * (sqrt(sa) + scal[0] * sqrt(sb));
   }
   __syncthreads();
   const double delta = s_delta;
-  for (int e = t; e < nn; e += blockDim.x) {
-    const int i = e % n, j = e / n;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)n * n) {
+    const int i = (int)(e % n), j = (int)(e / n);
     const double r = (i == j ? 1.0 : 0.0) - G[e];
     double out = 0.5 * r;
     if (i != j) {
-      const double di = S[i + (int64_t)i * n] / G[i + (int64_t)i * n];
-      const double dj = S[j + (int64_t)j * n] / G[j + (int64_t)j * n];
+      const double di = dvec[i], dj = dvec[j];
       const double gap = dj - di, num = S[e] + dj * r;
       if (fabs(gap) > delta && fabs(num) <= 1e-2 * fabs(gap)) out = num / gap;
     }
     E[e] = out;
   }
-  __syncthreads();
-  if (t == 0 && !(delta > 64.0 * n * kEps64 * scal[0])) done[0] = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    delta_out[0] = delta;
+    // converged: the update of this step and every later step are skipped
+    if (!(delta > 64.0 * n * kEps64 * scal[0])) done[0] = 1;
+  }
 }
 
 // Final pass on S = X^T A X, G = X^T X of the refined X (one CTA): order by
@@ -641,15 +852,15 @@ __global__ void __launch_bounds__(1024, 1) eig_finalize_kernel(int n, const doub
   if (lane == 0) red[warp] = b;
   __syncthreads();
   const double thr = 8.0 * kEps64 * scal[0];
-  if (t < n) {  // furthest sorted position coupled to position t
-    const int i = pm[t];
-    int rmax = t;
-    for (int j = 0; j < n; ++j) {
-      if (j == i) continue;
-      const double sij = S[i + (int64_t)j * n];
-      if (!(fabs(sij) <= thr)) rmax = max(rmax, pos[j]);
-    }
-    reach[t] = rmax;
+  // furthest sorted position coupled to each position (a warp per column of
+  // S, contiguous reads; S is symmetric to rounding)
+  for (int tt = warp; tt < n; tt += 32) {
+    const int i = pm[tt];
+    int rmax = tt;
+    for (int j = lane; j < n; j += 32)
+      if (j != i && !(fabs(S[j + (int64_t)i * n]) <= thr)) rmax = max(rmax, pos[j]);
+    for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (lane == 0) reach[tt] = rmax;
   }
   __syncthreads();
   if (t == 0) {
@@ -1155,7 +1366,7 @@ int DevDense::init(int64_t nmax_) {
   ok = ok && g((void**)&V32, nn * sizeof(float));
   ok = ok && g((void**)&Y32, nn * sizeof(float));
   ok = ok && g((void**)&f32v, 4 * (size_t)nmax * sizeof(float));
-  ok = ok && g((void**)&vec, 8 * (size_t)nmax * sizeof(double));
+  ok = ok && g((void**)&vec, (8 * (size_t)nmax + 256) * sizeof(double));
   ok = ok && g((void**)&scal, 16 * sizeof(double));
   ok = ok && g((void**)&ints, (4 * (size_t)nmax + 64) * sizeof(int));
   ok = ok && g((void**)&part, (size_t)tiles * kMaxKs * 256 * sizeof(double));
@@ -1237,12 +1448,15 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   if (dev >= 0 && dev < 64 && !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kDevDenseMax * (kDevDenseMax + 1) / 2 * 4));
+    LOB_CUDA_OK(cudaFuncSetAttribute(tridiag32_full_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kTridFull * (kTridFull | 1) * 4));
     LOB_CUDA_OK(cudaFuncSetAttribute(tridiag_eig_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (3 * kDevDenseMax + 6 * 32 * kDevDenseMax) * 4));
     LOB_CUDA_OK(cudaFuncSetAttribute(backtransform_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     16 * kDevDenseMax * 4));
+                                     (kDevDenseMax * (kDevDenseMax - 1) / 2 + 16 * kDevDenseMax) * 4));
     configured[dev] = true;
   }
   if (n == 1) {
@@ -1267,8 +1481,14 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   DLAUNCH(L);
   A = D.Zt;
   lda = n;
-  tridiag32_kernel<<<1, 1024, (size_t)n * (n + 1) / 2 * 4, L.st>>>(n, A, lda, d32, e32, D.V32, n,
-                                                                   tau32, normA);
+  if (n <= kTridFull)
+    tridiag32_full_kernel<<<1, 1024, (size_t)n * (n | 1) * 4, L.st>>>(n, A, lda, d32, e32, D.V32,
+                                                                      n, tau32, normA);
+  else
+    tridiag32_kernel<<<1, 1024, (size_t)n * (n + 1) / 2 * 4, L.st>>>(n, A, lda, d32, e32, D.V32,
+                                                                     n, tau32, normA);
+  DLAUNCH(L);
+  bisect_kernel<<<(unsigned)ceil_div(4 * n, 256), 256, 0, L.st>>>(n, d32, e32, lam32);
   DLAUNCH(L);
   tridiag_eig_kernel<<<(unsigned)ceil_div(n, 32), 32, (size_t)(3 * n + 6 * 32 * n) * 4, L.st>>>(
       n, d32, e32, lam32, D.Y32, n);
@@ -1279,7 +1499,8 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   double* X = D.XA;
   double* AX = D.XA + (size_t)n * n;
   double* G = D.GS;
-  backtransform_kernel<<<(unsigned)ceil_div(n, 16), 256, (size_t)16 * n * 4, L.st>>>(
+  backtransform_kernel<<<(unsigned)ceil_div(n, 16), 256,
+                         (size_t)((n * (n - 1)) / 2 + 16 * n) * 4, L.st>>>(
       n, D.V32, n, tau32, D.Y32, n, X, n);
   DLAUNCH(L);
   int rc;
@@ -1290,7 +1511,10 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
     if ((rc = dev_gemm(L, true, false, n, 2 * n, n, 1.0, X, n, D.XA, n, 0.0, nullptr, 0, G, n,
                        done)))
       return rc;
-    oa_step_kernel<<<1, 1024, 0, L.st>>>(n, D.GS, normA, D.E, done, delta);
+    oa_norms_kernel<<<kOaBlocks, 256, 0, L.st>>>(n, D.GS, D.vec, D.vec + 2 * kOaBlocks, done);
+    DLAUNCH(L);
+    oa_e_kernel<<<nblk((int64_t)n * n), 256, 0, L.st>>>(n, D.GS, D.vec, D.vec + 2 * kOaBlocks,
+                                                        normA, D.E, done, delta);
     DLAUNCH(L);
     // X1 = X + X E
     if ((rc = dev_gemm(L, false, false, n, n, n, 1.0, X, n, D.E, n, 1.0, X, n, D.X1, n, done)))
@@ -1407,6 +1631,13 @@ int read_flags(DenseLayer& L, const int* ints, int n_ints, const double* dbl, in
   return LOBPCG_OK;
 }
 
+// count the reasons of a failed check of the device eigensolver
+void note_check(DenseLayer& L, int mask) {
+  if (mask & 1) ++L.check_fail[0];
+  if (mask & 2) ++L.check_fail[1];
+  if (mask & 8) ++L.check_fail[2];
+}
+
 // Eigenvectors Z of H (order n) with eigenvalues in L.ev: device eigensolver,
 // its status read back with the other flags by the caller.
 int eig_into(DenseLayer& L, int n, const double* H, double* Z, int* status) {
@@ -1508,6 +1739,7 @@ int rr_initial_dev(DenseLayer& L, const double* GA, const double* GB, int nx, do
     *breakdown = true;
     return LOBPCG_OK;
   }
+  note_check(L, fl[1]);
   if (fl[1] != 0 && (rc = eig_fallback_into(L, nx, H, Z))) return rc;
   // C = D Ri Z
   if ((rc = dev_gemm(L, false, false, nx, nx, nx, 1.0, Ri, nx, Z, nx, 0.0, nullptr, 0, C, nx,
@@ -1552,6 +1784,7 @@ int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns,
     if ((rc = eig_into(L, ns, SAS, Z, est))) return rc;
     int fl[1];
     if ((rc = read_flags(L, est, 1, nullptr, 0, fl, nullptr))) return rc;
+    note_check(L, fl[0]);
     if (fl[0] != 0 && (rc = eig_fallback_into(L, ns, SAS, Z))) return rc;
     return rr_tail(L, Z, Z, ns, nx, nc, C, npn_out, theta, PAP);
   }
@@ -1599,6 +1832,7 @@ int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns,
     *flip = true;
     return LOBPCG_OK;
   }
+  note_check(L, fl[1]);
   if (fl[1] != 0 && (rc = eig_fallback_into(L, ns, Hsrc, Z))) return rc;
   // T Z = D ([Z_top; 0] + Y Z(o:, :))
   if (nw > 0) {
@@ -1632,6 +1866,7 @@ int svqb_transform_dev(DenseLayer& L, const double* G, int nu, bool drop, double
   DLAUNCH(L);
   int fl[2];
   if ((rc = read_flags(L, est, 2, nullptr, 0, fl, nullptr))) return rc;
+  note_check(L, fl[0]);
   if (fl[0] != 0) {
     if ((rc = eig_fallback_into(L, nu, MB, Z))) return rc;
     svqb_dev_kernel<<<1, 256, 0, L.st>>>(nu, L.ev, L.d, Z, nu, drop ? 1 : 0, tau, T, nu, keep);

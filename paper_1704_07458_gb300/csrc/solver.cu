@@ -465,6 +465,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   const int64_t eig0 = h->dense.eig_calls + h->dense.dev_calls,
                 eigf0 = h->dense.eig_fallbacks + h->dense.dev_fallbacks;
   const int64_t syncs0 = h->syncs + h->dense.syncs;
+  const int64_t cf0[3] = {h->dense.check_fail[0], h->dense.check_fail[1], h->dense.check_fail[2]};
   h->timer.st = h->st;
   h->timer.reset();
   h->timer.mark();
@@ -773,6 +774,9 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.eig_calls = h->dense.eig_calls + h->dense.dev_calls - eig0;
   h->stats.eig_fallbacks = h->dense.eig_fallbacks + h->dense.dev_fallbacks - eigf0;
   h->stats.host_syncs = h->syncs + h->dense.syncs - syncs0;
+  h->stats.eig_check_orthogonality = h->dense.check_fail[0] - cf0[0];
+  h->stats.eig_check_wide_cluster = h->dense.check_fail[1] - cf0[1];
+  h->stats.eig_check_nonfinite = h->dense.check_fail[2] - cf0[2];
   h->stats.ms_spmm = h->timer.total[PH_SPMM];
   h->stats.ms_gram = h->timer.total[PH_GRAM];
   h->stats.ms_update = h->timer.total[PH_UPDATE];

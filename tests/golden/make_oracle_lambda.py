@@ -52,10 +52,10 @@ def main():
                 f"# error (Eq. 9) {float(np.max(r.be)):.3e}, flip to orthogonalisation at iteration\n"
                 f"# {r.stats['flip_iter']}.\n")
         f.write(f"iterations {r.iters}\n")
-        f.write(f"norm_a {r.normA!r}\n")
-        f.write(f"norm_b {r.normB!r}\n")
+        f.write(f"norm_a {float(r.normA)!r}\n")
+        f.write(f"norm_b {float(r.normB)!r}\n")
         for i, (lam, be) in enumerate(zip(r.lam, r.be)):
-            f.write(f"lambda {i} {lam!r} {be!r}\n")
+            f.write(f"lambda {i} {float(lam)!r} {float(be)!r}\n")
     print(out, r.iters, "iterations", f"{dt:.0f} s")
 
 
