@@ -39,7 +39,9 @@ typedef enum {
   LOBPCG_ERR_BREAKDOWN = 3,      /* initial block numerically rank deficient (Alg. 2) */
   LOBPCG_ERR_CUDA = 4,           /* a CUDA, cuBLAS or cuSOLVER call failed */
   LOBPCG_ERR_OOM = 5,            /* device allocation failed */
-  LOBPCG_ERR_TIMEOUT = 6,        /* wall-clock limit of the options exceeded */
+  LOBPCG_ERR_TIMEOUT = 6,        /* wall-clock limit of the options exceeded, or a bounded
+                                    wait inside a tensor-core kernel ran out (its outputs are
+                                    then not valid; the context stays usable) */
   LOBPCG_ERR_CALLBACK = 7,       /* the preconditioner callback returned non-zero */
   LOBPCG_ERR_DEGENERATE = 8      /* lobpcg_eig_adjoint: two wanted eigenvalues coincide */
 } lobpcg_status;

@@ -837,11 +837,13 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
                         CUBLAS_DIAG_NON_UNIT, ns, ns, &one, Rm, ld, Q2, ld));
     {
       const size_t bytes = 3 * (size_t)ns * sizeof(float);
-      static bool configured = false;
-      if (!configured) {
+      static bool configured[64] = {false};  // the attribute is per device
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64 || !configured[dev]) {
         LOB_CUDA_OK(cudaFuncSetAttribute(cond_estimate_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        configured = true;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
       }
       if (bytes > 200 * 1024) return LOBPCG_ERR_ARG;
       cond_estimate_kernel<<<1, kCondThreads, bytes, L.st>>>(ns, Tz, ld, Q2, ld, L.scal);

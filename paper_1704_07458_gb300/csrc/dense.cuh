@@ -116,6 +116,7 @@ int dev_chol(DenseLayer& L, int n, double* A, int lda, int* info);
 int dev_trinv(DenseLayer& L, int n, const double* R, int ldr, double* X, int ldx, const int* skip);
 int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz, double* w,
              int* status);
+int dev_syev_refine(DenseLayer& L, int n, double* Z, int ldz, double* w, int* status, int steps);
 int dev_orth_basis(DenseLayer& L, int m, int c, const double* M, int ldm, double* Q, int ldq);
 bool dev_rr_fits(const DenseLayer& L, int ns, int nx, int nw);
 int rr_initial_dev(DenseLayer& L, const double* GA, const double* GB, int nx, double* C,

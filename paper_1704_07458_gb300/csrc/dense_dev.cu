@@ -1415,12 +1415,12 @@ int dev_chol(DenseLayer& L, int n, double* A, int lda, int* info) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kCholMax * kCholMax * 8));
     LOB_CUDA_OK(cudaFuncSetAttribute(trinv64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kCholMax * kCholMax * 8));
-    configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   chol64_kernel<<<1, 256, sh, L.st>>>(n, A, lda, info);
   DLAUNCH(L);
@@ -1445,7 +1445,7 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   int dev = 0;
   cudaGetDevice(&dev);
   static bool configured[64] = {false};
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(tridiag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kDevDenseMax * (kDevDenseMax + 1) / 2 * 4));
     LOB_CUDA_OK(cudaFuncSetAttribute(tridiag32_full_kernel,
@@ -1457,7 +1457,7 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
     LOB_CUDA_OK(cudaFuncSetAttribute(backtransform_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (kDevDenseMax * (kDevDenseMax - 1) / 2 + 16 * kDevDenseMax) * 4));
-    configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   if (n == 1) {
     eig1_kernel<<<1, 1, 0, L.st>>>(A, Z, w, status);
@@ -1468,13 +1468,7 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   float* e32 = D.f32v + D.nmax;
   float* tau32 = D.f32v + 2 * D.nmax;
   float* lam32 = D.f32v + 3 * D.nmax;
-  double* normA = D.scal;       // scal[0] = ||A||_F
-  double* delta = D.scal + 1;
-  int* done = D.ints;           // refinement converged flag
-  int* perm = D.ints + 4;
-  int* runs = perm + D.nmax;
-  int* nruns = runs + 2 * D.nmax;
-  LOB_CUDA_OK(cudaMemsetAsync(done, 0, sizeof(int), L.st));
+  double* normA = D.scal;  // scal[0] = ||A||_F
   // the refinement multiplies by the symmetric part of A (a projected
   // matrix formed by products is symmetric only to rounding)
   symmetrize_copy_kernel<<<nblk((int64_t)n * n), 256, 0, L.st>>>(n, A, lda, D.Zt, n);
@@ -1497,14 +1491,34 @@ int dev_syev(DenseLayer& L, int n, const double* A, int lda, double* Z, int ldz,
   DLAUNCH(L);
   // X (first n columns of XA) = Q Y
   double* X = D.XA;
-  double* AX = D.XA + (size_t)n * n;
-  double* G = D.GS;
   backtransform_kernel<<<(unsigned)ceil_div(n, 16), 256,
                          (size_t)((n * (n - 1)) / 2 + 16 * n) * 4, L.st>>>(
       n, D.V32, n, tau32, D.Y32, n, X, n);
   DLAUNCH(L);
+  return dev_syev_refine(L, n, Z, ldz, w, status, kRefSteps);
+}
+
+// Refinement of the current X (first block of D.XA) against the symmetric A
+// kept in D.Zt: `steps` Ogita-Aishima steps, two Newton-Schulz steps, the
+// final products, the finalize pass, the permutation into Z and Jacobi on
+// the coupled runs.  Also the second chance after a failed check: more
+// steps from where the first call stopped.
+int dev_syev_refine(DenseLayer& L, int n, double* Z, int ldz, double* w, int* status, int steps) {
+  DevDense& D = L.dev;
+  const double* A = D.Zt;
+  const int lda = n;
+  double* normA = D.scal;
+  double* delta = D.scal + 1;
+  int* done = D.ints;
+  int* perm = D.ints + 4;
+  int* runs = perm + D.nmax;
+  int* nruns = runs + 2 * D.nmax;
+  double* X = D.XA;
+  double* AX = D.XA + (size_t)n * n;
+  double* G = D.GS;
+  LOB_CUDA_OK(cudaMemsetAsync(done, 0, sizeof(int), L.st));
   int rc;
-  for (int s = 0; s < kRefSteps; ++s) {
+  for (int s = 0; s < steps; ++s) {
     // [G, S] = X^T [X, A X]
     if ((rc = dev_gemm(L, false, false, n, n, n, 1.0, A, lda, X, n, 0.0, nullptr, 0, AX, n, done)))
       return rc;
@@ -1557,10 +1571,10 @@ int dev_orth_basis(DenseLayer& L, int m, int c, const double* M, int ldm, double
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(qr32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      200 * 1024));
-    configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   const size_t sh = 2 * (size_t)m * c * sizeof(float);
   if (sh > 200 * 1024 || c > 256) return LOBPCG_ERR_ARG;
@@ -1608,10 +1622,10 @@ int configure_cond(DenseLayer& L) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(cond_struct_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   (void)L;
   return LOBPCG_OK;
@@ -1645,12 +1659,27 @@ int eig_into(DenseLayer& L, int n, const double* H, double* Z, int* status) {
   return dev_syev(L, n, H, n, Z, n, L.ev, status);
 }
 
-// Fallback after a failed device eigensolve: cuSOLVER on a copy of H.
-int eig_fallback_into(DenseLayer& L, int n, const double* H, double* Z) {
+// After a failed check: when only the coupled groups were too wide, three
+// more refinement steps from where the first call stopped (one more host
+// read); otherwise, or when that fails too, cuSOLVER on a copy of H.
+int eig_recover(DenseLayer& L, int n, const double* H, double* Z, int mask) {
+  int rc;
+  if (mask == 2) {
+    int* est = L.dev.ints + 2;
+    if ((rc = dev_syev_refine(L, n, Z, n, L.ev, est, 3))) return rc;
+    int fl = 0;
+    LOB_CUDA_OK(cudaMemcpyAsync(L.host, est, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+    LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+    ++L.syncs;
+    memcpy(&fl, L.host, sizeof(int));
+    if (fl == 0) return LOBPCG_OK;
+    note_check(L, fl);
+  }
   copy_block_cm_kernel<<<nblk((int64_t)n * n), 256, 0, L.st>>>(n, n, H, n, Z, n, 1.0);
   DLAUNCH(L);
   return syevd_fallback(L, n, Z, n);
 }
+
 
 // C = [C_x, C_p] and the next P^T A P from T Z (ns x ns), Z and the
 // eigenvalues L.ev (Algorithm 7, the LQ-based C_p of Sec. 4.2 restricted to
@@ -1740,7 +1769,7 @@ int rr_initial_dev(DenseLayer& L, const double* GA, const double* GB, int nx, do
     return LOBPCG_OK;
   }
   note_check(L, fl[1]);
-  if (fl[1] != 0 && (rc = eig_fallback_into(L, nx, H, Z))) return rc;
+  if (fl[1] != 0 && (rc = eig_recover(L, nx, H, Z, fl[1]))) return rc;
   // C = D Ri Z
   if ((rc = dev_gemm(L, false, false, nx, nx, nx, 1.0, Ri, nx, Z, nx, 0.0, nullptr, 0, C, nx,
                      nullptr)))
@@ -1785,7 +1814,7 @@ int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns,
     int fl[1];
     if ((rc = read_flags(L, est, 1, nullptr, 0, fl, nullptr))) return rc;
     note_check(L, fl[0]);
-    if (fl[0] != 0 && (rc = eig_fallback_into(L, ns, SAS, Z))) return rc;
+    if (fl[0] != 0 && (rc = eig_recover(L, ns, SAS, Z, fl[0]))) return rc;
     return rr_tail(L, Z, Z, ns, nx, nc, C, npn_out, theta, PAP);
   }
   dscale2_kernel<<<nblk((int64_t)ns * ns), 256, 0, L.st>>>(ns, SBS, ns, SAS, ns, L.d, MB, MA, ns);
@@ -1833,7 +1862,7 @@ int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns,
     return LOBPCG_OK;
   }
   note_check(L, fl[1]);
-  if (fl[1] != 0 && (rc = eig_fallback_into(L, ns, Hsrc, Z))) return rc;
+  if (fl[1] != 0 && (rc = eig_recover(L, ns, Hsrc, Z, fl[1]))) return rc;
   // T Z = D ([Z_top; 0] + Y Z(o:, :))
   if (nw > 0) {
     if ((rc = dev_gemm(L, false, false, ns, ns, nw, 1.0, Y, ns, Z + o, ns, 0.0, nullptr, 0, TZ, ns,
@@ -1868,7 +1897,7 @@ int svqb_transform_dev(DenseLayer& L, const double* G, int nu, bool drop, double
   if ((rc = read_flags(L, est, 2, nullptr, 0, fl, nullptr))) return rc;
   note_check(L, fl[0]);
   if (fl[0] != 0) {
-    if ((rc = eig_fallback_into(L, nu, MB, Z))) return rc;
+    if ((rc = eig_recover(L, nu, MB, Z, fl[0]))) return rc;
     svqb_dev_kernel<<<1, 256, 0, L.st>>>(nu, L.ev, L.d, Z, nu, drop ? 1 : 0, tau, T, nu, keep);
     DLAUNCH(L);
     if ((rc = read_flags(L, keep, 1, nullptr, 0, fl + 1, nullptr))) return rc;

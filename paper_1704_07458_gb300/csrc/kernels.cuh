@@ -31,9 +31,12 @@ int gram_tc(cudaStream_t st, int64_t n, const SegList& U, const SegList& V, doub
 
 // Y = beta Y0 + alpha S C on tcgen05 (beta 0 or 1), colexp as update_ozaki.
 int64_t update_tc_workspace(int64_t n, int s, int m, int slices);
+// status (device int, may be null): bit 0 set when a bounded wait of the
+// tensor-core kernel ran out (its outputs are then not valid).
 int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc, int m,
               double alpha, double beta, const SegList& Y0, const OutList& Y, int slices,
-              void* work, int64_t work_bytes, const int* colexp = nullptr);
+              void* work, int64_t work_bytes, const int* colexp = nullptr,
+              int* status = nullptr);
 
 // colexp[k] = E with max_i |S(i, k)| < 2^E over an n x s block (0 for zero columns).
 int column_exponents(cudaStream_t st, int64_t n, const SegList& Sg, int s, int* out);

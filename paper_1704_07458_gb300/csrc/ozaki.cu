@@ -504,11 +504,13 @@ template <int S>
 int gram_launch(cudaStream_t st, int64_t n, const SegList& U, int p, const SegList& V, int q,
                 int slabs, int64_t rps, float4* partial) {
   const size_t sh = stage_bytes<S>();
-  static bool configured = false;
-  if (!configured) {
+  static bool configured[64] = {false};  // the attribute is per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_gram_kernel<S>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    configured = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   dim3 grid((unsigned)ceil_div(p, TM), (unsigned)ceil_div(q, TN), (unsigned)slabs);
   ozaki_gram_kernel<S><<<grid, kThreads, sh, st>>>(n, U, p, V, q, rps, partial);
@@ -537,11 +539,13 @@ int update_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const do
     LOB_LAUNCHED();
   }
   const size_t sh = stage_bytes<S>();
-  static bool configured = false;
-  if (!configured) {
+  static bool configured[64] = {false};  // the attribute is per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_kernel<S>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    configured = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   const int64_t blocks = (int64_t)(mpad / TN) * ceil_div(n, TM);
   ozaki_update_kernel<S><<<(unsigned)blocks, kThreads, sh, st>>>(n, Sg, s, colexp, Cs, Ce, m,

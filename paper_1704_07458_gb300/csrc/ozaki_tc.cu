@@ -29,7 +29,8 @@
 //    (per 256-row block and column for the Gram, per row for the update), so
 //    the tensor-core kernels never wait on a global load of their own;
 //  * every mbarrier wait is bounded: a wait that runs out marks the result NaN
-//    and the CTA returns instead of hanging.
+//    (and, for the update, sets a status bit that the solver reads with its
+//    per-iteration scalars) and the CTA returns instead of hanging.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -624,11 +625,13 @@ int gram_tc_launch(cudaStream_t st, int64_t n, const SegList& U, int p, const Se
   int ntq, NT;
   gram_tiles(q, &ntq, &NT);
   const size_t sh = gram_smem_bytes<S>(NTMAX);
-  static bool configured = false;
-  if (!configured) {
+  static bool configured[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_gram_tc_kernel<S>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    configured = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   dim3 grid((unsigned)ceil_div(p, TCM), (unsigned)ntq, (unsigned)slabs);
   ozaki_gram_tc_kernel<S><<<grid, kThr, gram_smem_bytes<S>(NT), st>>>(n, U, p, V, q, NT, per, EU,
@@ -778,7 +781,8 @@ __global__ void __launch_bounds__(kThrAll, 1)
     ozaki_update_tc_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
                            const uint16_t* __restrict__ Cs, const int* __restrict__ Ce,
                            const int* __restrict__ ER, int m, int ntiles, int NT,
-                           int64_t ntile_total, double beta, SegList Y0, OutList Y) {
+                           int64_t ntile_total, double beta, SegList Y0, OutList Y,
+                           int* status) {
   constexpr int NA = nacc<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -1018,6 +1022,7 @@ __global__ void __launch_bounds__(kThrAll, 1)
     }
   }
   if (compute) cp_async_wait0();  // no copy may outlive the CTA
+  if (tid == 0 && failed && status) atomicOr(status, 1);
   if (tid == kIssuerW && b_issued >= 0 && failed)
     mbar_wait(smem_u32(&sh.bfull[b_issued & 1]), (uint32_t)(b_issued >> 1) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -1036,7 +1041,7 @@ void update_tiles(int m, int* ntiles, int* NT) {
 template <int S>
 int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const double* C,
                      int64_t ldc, int m, double alpha, double beta, const SegList& Y0,
-                     const OutList& Y, const int* colexp, void* work) {
+                     const OutList& Y, const int* colexp, void* work, int* status) {
   int ntiles, NT;
   update_tiles(m, &ntiles, &NT);
   const int nch = (int)ceil_div(s, TCK);
@@ -1059,22 +1064,25 @@ int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const
     LOB_LAUNCHED();
   }
   const size_t shmax = upd_smem_bytes<S>(NTMAX, kMaxUpdateK);
-  static bool configured = false;
-  if (!configured) {
+  // the attribute is per device: set it once on every device that launches
+  static bool configured[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
     LOB_CUDA_OK(cudaFuncSetAttribute(ozaki_update_tc_kernel<S, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
-    configured = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   const int64_t tiles = ceil_div(n, TCM) * ntiles;
   const int64_t grid = std::min<int64_t>(tiles, 152);
   if (s <= kBlock)
     ozaki_update_tc_kernel<S, true><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
-        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y);
+        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y, status);
   else
     ozaki_update_tc_kernel<S, false><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
-        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y);
+        n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y, status);
   LOB_LAUNCHED();
   return LOBPCG_OK;
 }
@@ -1137,7 +1145,7 @@ int64_t update_tc_workspace(int64_t n, int s, int m, int slices) {
 
 int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int64_t ldc, int m,
               double alpha, double beta, const SegList& Y0, const OutList& Y, int slices,
-              void* work, int64_t work_bytes, const int* colexp) {
+              void* work, int64_t work_bytes, const int* colexp, int* status) {
   const int s = S.off[S.nseg];
   if (n <= 0 || m <= 0) return LOBPCG_OK;
   if (slices == 0) slices = 6;
@@ -1146,11 +1154,11 @@ int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int
   if (work_bytes < update_tc_workspace(n, s, m, slices)) return LOBPCG_ERR_ARG;
   if (beta != 0.0 && beta != 1.0) return LOBPCG_ERR_ARG;
   switch (slices) {
-    case 3: return update_tc_launch<3>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
-    case 4: return update_tc_launch<4>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
-    case 5: return update_tc_launch<5>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
-    case 6: return update_tc_launch<6>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
-    case 7: return update_tc_launch<7>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work);
+    case 3: return update_tc_launch<3>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work, status);
+    case 4: return update_tc_launch<4>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work, status);
+    case 5: return update_tc_launch<5>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work, status);
+    case 6: return update_tc_launch<6>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work, status);
+    case 7: return update_tc_launch<7>(st, n, S, s, C, ldc, m, alpha, beta, Y0, Y, colexp, work, status);
     default: return LOBPCG_ERR_ARG;
   }
 }

@@ -126,6 +126,7 @@ struct lobpcg_ctx {
   double* kinv = nullptr;  // 1 / diag(K) for the current solve (n)
   int slice_boost = 0;     // 7 once a solve in an emulated form has stalled
   int *cexp, *zexp;  // column balance exponents of S, and all zeros
+  int* dstatus = nullptr;  // device status word of the tensor-core kernels (bit 0: a wait ran out)
   void* gwork = nullptr;
   int64_t gwork_bytes = 0;
   void* uwork = nullptr;
@@ -219,6 +220,7 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   if ((rc = dalloc(h, (void**)&h->kinv, (size_t)n * sizeof(double)))) return rc;
   if ((rc = dalloc(h, (void**)&h->cexp, (size_t)nsmax * sizeof(int)))) return rc;
   if ((rc = dalloc(h, (void**)&h->zexp, (size_t)nsmax * sizeof(int)))) return rc;
+  if ((rc = dalloc(h, (void**)&h->dstatus, 16))) return rc;
   LOB_CUDA_OK(cudaMemsetAsync(h->zexp, 0, (size_t)nsmax * sizeof(int), h->st));
   // Gram scratch: the widest use is S^T [AW, BW] (3 nx x 2 nx) or X^T [AX, BX].
   const int mode = gemm_mode(h), sl = slices(h);
@@ -290,7 +292,8 @@ int update(lobpcg_ctx* h, const SegList& S, const double* C, int64_t ldc, int m,
   }
   if (gemm_mode(h) == LOBPCG_GEMM_OZAKI_TC)
     return update_tc(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
-                     std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);
+                     std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp,
+                     h->dstatus);
   if (gemm_mode(h))
     return update_ozaki(h->st, h->n, S, C, ldc, m, alpha, beta, Y0, Y,
                         std::max(slices(h), min_slices), h->uwork, h->uwork_bytes, colexp);
@@ -332,6 +335,24 @@ int to_host(lobpcg_ctx* h, double* dst, const double* src, int64_t count) {
   memcpy(dst, h->hbuf, count * sizeof(double));
   h->timer.flush();
   return LOBPCG_OK;
+}
+
+// Backward errors of the current iterate and the tensor-core status word in
+// one host wait; a bounded wait that ran out in a tensor-core kernel turns
+// into LOBPCG_ERR_TIMEOUT (its outputs are not valid).
+int read_be(lobpcg_ctx* h, double* dst, int64_t count) {
+  if (count > 0)
+    LOB_CUDA_OK(cudaMemcpyAsync(h->hbuf, h->be, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->st));
+  LOB_CUDA_OK(cudaMemcpyAsync(h->hbuf + std::max<int64_t>(count, 0) + 1, h->dstatus, sizeof(int),
+                              cudaMemcpyDeviceToHost, h->st));
+  LOB_CUDA_OK(cudaStreamSynchronize(h->st));
+  ++h->syncs;
+  if (count > 0) memcpy(dst, h->hbuf, count * sizeof(double));
+  int stw = 0;
+  memcpy(&stw, h->hbuf + std::max<int64_t>(count, 0) + 1, sizeof(int));
+  h->timer.flush();
+  return stw ? h->fail(LOBPCG_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out") : 0;
 }
 
 int sum_sq_norms(lobpcg_ctx* h, const double* Y, int m, double* out) {
@@ -460,6 +481,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->slice_boost = 0;
   int rc = ensure_workspace(h, nx);
   if (rc) return h->fail(rc, "workspace allocation failed");
+  LOB_CUDA_OK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
   const auto t_start = std::chrono::steady_clock::now();
   const int64_t launches0 = g_launches;
   const int64_t eig0 = h->dense.eig_calls + h->dense.dev_calls,
@@ -579,7 +601,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   };
   Wbase = h->wbuf[0];
   if ((rc = residual_step(0, true))) return rc;
-  if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
+  if ((rc = read_be(h, be_h.data(), nx))) return rc;
   nc = std::min<int64_t>(leading_converged(be_h.data(), nx, tol), nx);
   if ((rc = finish_w(0, nc))) return h->fail(rc, "preconditioner callback failed");
 
@@ -696,7 +718,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       // Algorithm 8: residual, preconditioned W and the convergence test
       Wbase = (Wbase == h->wbuf[0]) ? h->wbuf[1] : h->wbuf[0];
       if ((rc = residual_step(nc, true))) return rc;
-      if ((rc = to_host(h, be_h.data(), h->be, nx - nc))) return rc;
+      if ((rc = read_be(h, be_h.data(), nx - nc))) return rc;
       const int64_t ncn = std::max(nc, nc + leading_converged(be_h.data(), nx - nc, tol));
       refresh_next = ncn > nc;
       // Stall guard of the emulated forms: when over kStallWindow iterations
@@ -723,7 +745,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
     // exit certification: explicit products and Eq. (9) again
     if ((rc = apply_AB(h, h->X, (int)nx, h->AX, h->BX))) return rc;
     if ((rc = residual_step(0, false))) return rc;
-    if ((rc = to_host(h, be_h.data(), h->be, nx))) return rc;
+    if ((rc = read_be(h, be_h.data(), nx))) return rc;
     const int64_t good = leading_converged(be_h.data(), nx, tol);
     if (good >= k) break;
     nc = good;
