@@ -88,6 +88,23 @@ typedef struct {
                              1 FP32 cuSOLVER syevd refined to FP64 (Ogita-Aishima steps,
                              Newton-Schulz, cluster Jacobi; FP64 syevd when its residual
                              check fails); 2 cuSOLVER FP64 syevd and cuBLAS throughout */
+  int32_t basis;          /* basis selection: 0 Algorithm 8 (orthoDrop when cond(R) demands it,
+                             LQ-based C_p, Gram identities (12)-(14));  the comparison variants
+                             of Sec. 6, with the Hetmaniuk-Lehoucq basis selection (W
+                             B-orthogonalised against [X, P] by Algorithm 3 on every iteration,
+                             C_p of Eq. 6 orthonormalised by svqb, standard eigenproblem):
+                             1 CHL (no implicit products, every Gram block computed),
+                             2 AHL (implicit products, only (12) assumed) */
+  int32_t explicit_rr;    /* 0 auto (on in the emulated forms), 1 off, 2 on: on the iteration
+                             after each explicit refresh of A X, A P the projected pencil is
+                             formed from explicit Grams of every block instead of the
+                             identities (12)-(14), which the updates' rounding erodes */
+  int32_t criterion;      /* convergence test: 0 or 9 the backward error of Eq. (9); 7 and 8
+                             the relative residuals (7), (8) of Sec. 4.3 (contrast studies) */
+  int32_t gram_blocks;    /* blocks of the projected pencil taken from identities instead of
+                             computed (basis 0): 0 all of (12)-(14) (Algorithm 8); 1 only (12)
+                             (X^T A X = Theta, X^T B X = I; the P blocks are computed); 2 none
+                             (the versions study of Sec. 6.2) */
 } lobpcg_options_t;
 
 /* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
@@ -140,6 +157,8 @@ typedef struct {
    * coupled eigenvalues was wider than its cluster Jacobi takes (32), or a
    * value was not finite (a call may count under several) */
   int64_t eig_check_orthogonality, eig_check_wide_cluster, eig_check_nonfinite;
+  /* iterations whose projected pencil came from explicit Grams of every block */
+  int64_t explicit_rr_calls;
 } lobpcg_stats_t;
 
 /* Preconditioner callback: write W = K^-1 R for an n x ncols row-major block.
@@ -148,6 +167,28 @@ typedef struct {
  * LOBPCG_ERR_CALLBACK. */
 typedef int (*lobpcg_precond_fn)(void* ctx, int64_t n, int64_t ncols, const double* R,
                                  int64_t ldr, double* W, int64_t ldw, void* stream);
+
+/* Chebyshev polynomial preconditioner for the callback slot (Algorithm 1,
+ * Eq. 2 admit any preconditioner K).  K^-1 R is `degree` steps of the
+ * Chebyshev iteration for A W = R from W = 0 with the Jacobi splitting
+ * D = diag(A) and the spectral interval [lmin, lmax] of D^-1 A (Saad,
+ * Iterative Methods for Sparse Linear Systems, Algorithm 12.1), i.e.
+ * W = p(D^-1 A) D^-1 R for a fixed polynomial p positive on the interval, so
+ * K is symmetric positive definite.  rowptr, col, val: device CSR of A,
+ * borrowed (they must outlive the object); diag: device diag(A) or NULL
+ * (taken from the CSR); max_cols: the widest block it will be applied to
+ * (the solver's block width).  Allocates 3 n x max_cols work blocks.
+ * lobpcg_chebyshev_apply has the lobpcg_precond_fn signature:
+ *   lobpcg_set_precond_callback(h, lobpcg_chebyshev_apply, cheb);
+ * Errors: LOBPCG_ERR_ARG (degree outside 1..64, 0 < lmin < lmax violated,
+ * ncols > max_cols or n different from the object's), LOBPCG_ERR_OOM. */
+typedef struct lobpcg_chebyshev* lobpcg_chebyshev_t;
+int lobpcg_chebyshev_create(lobpcg_chebyshev_t* out, int64_t n, const int32_t* rowptr,
+                            const int32_t* col, const double* val, const double* diag, int degree,
+                            double lmin, double lmax, int64_t max_cols);
+int lobpcg_chebyshev_apply(void* ctx, int64_t n, int64_t ncols, const double* R, int64_t ldr,
+                           double* W, int64_t ldw, void* stream);
+void lobpcg_chebyshev_destroy(lobpcg_chebyshev_t c);
 
 /* Create a handle bound to the current CUDA device and `stream`.  opts may be
  * NULL (defaults).  The handle owns every device buffer it allocates. */

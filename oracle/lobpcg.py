@@ -16,6 +16,13 @@ implementation of LOBPCG", 2018):
   lobpcg                   Algorithm 8 with soft locking (Sec. 3), the Gram
                            identities (12)-(14) and implicit product updates
                            (Sec. 5.2, Eq. 10-11)
+  ortho                    Algorithm 3 (Stathopoulos-Wu block orthogonalisation)
+  rayleigh_ritz_hl         the Rayleigh-Ritz step of the Hetmaniuk-Lehoucq
+                           basis selection with C_p of Eq. (6)
+  lobpcg(basis="chl"/"ahl") the comparison variants of Sec. 6: HL basis
+                           selection every iteration, conservative (CHL: no
+                           implicit updates, every Gram block computed) or
+                           aggressive (AHL: implicit updates, only (12) assumed)
 
 Readings where the paper is silent or inconsistent (each is a documented
 choice, identical in the CUDA library):
@@ -73,8 +80,9 @@ class Pencil:
     Sparse products use scipy.sparse as a library primitive.
     """
 
-    def __init__(self, n, A, B=None, kdiag=None):
+    def __init__(self, n, A, B=None, kdiag=None, k_fn=None):
         self.n = n
+        self.k_fn = k_fn  # a general K^-1 (callable on a block), e.g. chebyshev_precond
         self.A = sp.csr_matrix((A[2], A[1], A[0]), shape=(n, n))
         if B is None:
             self.b_kind = "identity"
@@ -97,6 +105,8 @@ class Pencil:
         return np.asarray(self.B @ X)
 
     def K_inv(self, R):
+        if self.k_fn is not None:
+            return self.k_fn(R)
         if self.kdiag is None:
             return R.copy()
         return R / self.kdiag[:, None]
@@ -109,6 +119,30 @@ class Pencil:
             b = np.abs(self.b)
             return b.min() > 0 and b.max() / b.min() <= 1e4
         return False
+
+
+def chebyshev_precond(A, degree, lmin, lmax):
+    """K^-1 R = `degree` steps of the Chebyshev iteration for A W = R from
+    W = 0 with the Jacobi splitting D = diag(A) and the spectral interval
+    [lmin, lmax] of D^-1 A (Saad, Iterative Methods for Sparse Linear Systems,
+    Algorithm 12.1).  A: scipy CSR.  Returns the callable R -> W."""
+    dinv = 1.0 / A.diagonal()
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sigma = theta / delta
+
+    def apply(R):
+        rho = 1.0 / sigma
+        d = dinv[:, None] * R / theta
+        w = d.copy()
+        for _ in range(1, degree):
+            z = dinv[:, None] * (R - A @ w)
+            rho1 = 1.0 / (2.0 * sigma - rho)
+            d = rho1 * rho * d + (2.0 * rho1 / delta) * z
+            w = w + d
+            rho = rho1
+        return w
+    return apply
 
 
 # --------------------------------------------------------------------------
@@ -239,6 +273,53 @@ def ortho_drop(B_mul, U, V, BV, tau_ortho, stats=None, itmax1=3, itmax2=3):
     return U, BU
 
 
+def ortho(B_mul, U, V, BV, tau_ortho, stats=None, itmax1=3, itmax2=3):
+    """Algorithm 3 (Stathopoulos-Wu): B-orthonormalise U against V with block
+    classical Gram-Schmidt and inner svqb passes (Algorithm 4, no dropping:
+    the column count never changes).  Returns (U, BU)."""
+    BU = B_mul(U)
+    nu = U.shape[1]
+    for i in range(itmax1):
+        if V.shape[1] > 0:
+            U = U - V @ (BV.T @ U)
+        for j in range(itmax2):
+            BU = B_mul(U)
+            U = svqb(U, BU, nu * EPS)
+            if stats is not None:
+                stats["svqb_passes"] += 1
+            BU = B_mul(U)
+            if U.shape[1] == 0:
+                return U, BU
+            G = U.T @ BU
+            err = np.linalg.norm(G - np.eye(U.shape[1])) / (
+                np.linalg.norm(BU) * np.linalg.norm(U))
+            if err <= tau_ortho:
+                break
+        if V.shape[1] == 0:
+            break
+        err = np.linalg.norm(BV.T @ U) / (np.linalg.norm(BV) * np.linalg.norm(U))
+        if err <= tau_ortho:
+            break
+    return U, BU
+
+
+def rayleigh_ritz_hl(SAS, nx, nc):
+    """Rayleigh-Ritz of the Hetmaniuk-Lehoucq basis selection: S is
+    B-orthonormal, so eig(S^T A S) = Z Theta Z^T gives C_x = Z(:, :n_x); C_p
+    orthonormalises [0; Z_2] - Z_x Z_x^T [0; Z_2] (Eq. 6, restricted to the
+    unlocked columns n_c:n_x) with svqb in the Euclidean metric; P^T A P is
+    then C_p^T S^T A S C_p (the P block no longer lies in the Ritz basis)."""
+    ns = SAS.shape[0]
+    theta, Z = dense.eigh(SAS)
+    Zx = Z[:, :nx]
+    Y = np.zeros((ns, nx - nc))
+    Y[nx:, :] = Zx[nx:, nc:nx]
+    Y = Y - Zx @ (Zx.T @ Y)
+    Cp = svqb(Y, Y, max(Y.shape[1], 1) * EPS) if Y.shape[1] else Y
+    PAP = Cp.T @ SAS @ Cp
+    return RRResult(Zx, Cp, theta[:nx].copy(), 0.5 * (PAP + PAP.T), False, 1.0)
+
+
 # --------------------------------------------------------------------------
 # Algorithm 7
 
@@ -302,6 +383,7 @@ class Options:
     refresh_every: int = 50
     direct_gram: bool = False     # compute every block of S^T A S, S^T B S
     certify: bool = True
+    basis: str = "robust"         # robust (Algorithm 8) | chl | ahl (Sec. 6 comparisons)
 
 
 @dataclass
@@ -343,6 +425,7 @@ def sign_normalise(X):
 def lobpcg(pencil, X0, k, tol, Omega, opts=None):
     """Algorithm 8 on the pencil; X0 is n x n_x.  Returns a Result."""
     opts = opts or Options()
+    hl = opts.basis in ("chl", "ahl")
     n, nx = X0.shape
     stats = {"flip_iter": None, "ortho_calls": 0, "svqb_passes": 0,
              "dropped": 0, "nc_history": [], "condR": []}
@@ -350,6 +433,8 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
     normB = 1.0 if pencil.b_kind == "identity" else norm_estimate(pencil.B_mul, Omega)
     implicit = {"auto": pencil.implicit_allowed(), "always": True,
                 "never": False}[opts.implicit]
+    if opts.basis == "chl":
+        implicit = False  # conservative: every product explicit
 
     # Algorithm 8, initial step: Rayleigh-Ritz on X0 (Algorithm 2)
     AX0, BX0 = pencil.A_mul(X0), pencil.B_mul(X0)
@@ -362,7 +447,7 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
     theta = theta[:nx]
     P = np.zeros((n, 0)); AP = np.zeros((n, 0)); BP = np.zeros((n, 0))
     PAP = np.zeros((0, 0))
-    use_ortho = False
+    use_ortho = hl  # the HL variants orthogonalise W on every iteration
     R = AX - BX * theta[None, :]
     be = backward_error(R, X, theta, normA, normB)
     nc = min(leading_converged(be, tol), nx)
@@ -379,9 +464,12 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
             V = np.hstack([X, P])
             BV = np.hstack([BX, BP])
 
-            def make_w(ortho):
+            def make_w(do_ortho):
                 W0 = pencil.K_inv(R[:, nc:])
-                if ortho:
+                if do_ortho and hl:
+                    stats["ortho_calls"] += 1
+                    W, BW = ortho(pencil.B_mul, W0, V, BV, opts.tau_ortho, stats)
+                elif do_ortho:
                     stats["ortho_calls"] += 1
                     W, BW = ortho_drop(pencil.B_mul, W0, V, BV, opts.tau_ortho, stats)
                     stats["dropped"] += W0.shape[1] - W.shape[1]
@@ -391,7 +479,23 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
 
             def project(W, AW, BW):
                 S = np.hstack([X, P, W])
-                if opts.direct_gram:
+                if opts.basis == "ahl":
+                    # (12) holds: X^T A X = Theta, X^T B X = I; every block
+                    # with P or W is computed from the (implicit) products
+                    ns_ = S.shape[1]
+                    PW = np.hstack([P, W])
+                    APW = np.hstack([AP, AW])
+                    BPW = np.hstack([BP, BW])
+                    SAS = np.zeros((ns_, ns_))
+                    SBS = np.zeros((ns_, ns_))
+                    SAS[:nx, :nx] = np.diag(theta)
+                    SBS[:nx, :nx] = np.eye(nx)
+                    SAS[:, nx:] = S.T @ APW
+                    SBS[:, nx:] = S.T @ BPW
+                    SAS[nx:, :nx] = SAS[:nx, nx:].T
+                    SBS[nx:, :nx] = SBS[:nx, nx:].T
+                    return 0.5 * (SAS + SAS.T), 0.5 * (SBS + SBS.T)
+                if opts.direct_gram or opts.basis == "chl":
                     AS = np.hstack([AX, AP, AW]) if not implicit else np.hstack(
                         [pencil.A_mul(X), pencil.A_mul(P), AW])
                     BS = pencil.B_mul(S)
@@ -401,7 +505,10 @@ def lobpcg(pencil, X0, k, tol, Omega, opts=None):
 
             W, BW, AW = make_w(use_ortho)
             SAS, SBS = project(W, AW, BW)
-            rr = rayleigh_ritz_modified(SAS, SBS, nx, nc, use_ortho, opts.tau_skip)
+            if hl:
+                rr = rayleigh_ritz_hl(SAS, nx, nc)
+            else:
+                rr = rayleigh_ritz_modified(SAS, SBS, nx, nc, use_ortho, opts.tau_skip)
             stats["condR"].append(rr.condR)
             if rr.flip:
                 # Algorithm 8: switch to orthogonalisation and project again

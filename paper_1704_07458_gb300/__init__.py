@@ -25,6 +25,7 @@ from ._native import (  # noqa: F401
     lobpcg_destroy, lobpcg_spmm, lobpcg_gram, lobpcg_gram_workspace, lobpcg_gram_noalloc,
     lobpcg_update, lobpcg_eig_adjoint, lobpcg_syev,
     lobpcg_residual, lobpcg_philox_normal, load, library_path,
+    lobpcg_chebyshev_create, lobpcg_chebyshev_apply, lobpcg_chebyshev_destroy,
 )
 
 __all__ = [n for n in dir() if n.startswith("lobpcg_") or n.startswith("LOBPCG_")] + [
@@ -40,6 +41,10 @@ def options(**kw):
                  "ozaki_tc": LOBPCG_GEMM_OZAKI_TC}[v]
         if k == "implicit" and isinstance(v, str):
             v = {"auto": 0, "never": 1, "always": 2}[v]
+        if k == "basis" and isinstance(v, str):
+            v = {"robust": 0, "chl": 1, "ahl": 2}[v]
+        if k == "explicit_rr" and isinstance(v, str):
+            v = {"auto": 0, "off": 1, "on": 2}[v]
         setattr(o, k, v)
     return o
 
@@ -57,11 +62,15 @@ class Solver:
         self.h = lobpcg_create(self.opts, stream)
         self.n = 0
         self._cb = None
+        self._cheb = None
 
     def close(self):
         if self.h:
             lobpcg_destroy(self.h)
             self.h = None
+        if getattr(self, "_cheb", None) is not None:
+            lobpcg_chebyshev_destroy(self._cheb)
+            self._cheb = None
 
     def __del__(self):
         try:
@@ -150,6 +159,20 @@ class Solver:
                 return 1
         self._cb = _native.PRECOND_FN(tramp)
         self._check(lobpcg_set_precond_callback(self.h, self._cb, None), "set_precond_callback")
+
+    def set_precond_chebyshev(self, rowptr, col, val, degree, lmin, lmax, max_cols,
+                              diag=None):
+        """K^-1 = `degree` Chebyshev steps for A (device CSR tensors, kept
+        alive by this object) over the interval [lmin, lmax] of D^-1 A, applied
+        by the library through its callback slot (lobpcg_chebyshev_apply)."""
+        if self._cheb is not None:
+            lobpcg_chebyshev_destroy(self._cheb)
+        self._cheb_refs = (rowptr, col, val, diag)
+        self._cheb = lobpcg_chebyshev_create(self.n, rowptr, col, val, diag, degree, lmin, lmax,
+                                             max_cols)
+        self._cb = _native.chebyshev_callback()
+        self._check(lobpcg_set_precond_callback(self.h, self._cb, self._cheb),
+                    "set_precond_callback")
 
     def solve(self, k, tol=1e-8, X0=None, seed=0, device=False, raise_on_error=True):
         """Return (lam, X, iters, backward_errors, status).

@@ -34,6 +34,7 @@ EXPORTED = [
     "lobpcg_destroy", "lobpcg_spmm", "lobpcg_gram", "lobpcg_gram_workspace",
     "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
     "lobpcg_eig_adjoint", "lobpcg_syev",
+    "lobpcg_chebyshev_create", "lobpcg_chebyshev_apply", "lobpcg_chebyshev_destroy",
 ]
 
 
@@ -51,6 +52,10 @@ class lobpcg_options_t(ctypes.Structure):
         ("tau_skip", ctypes.c_double),
         ("max_seconds", ctypes.c_double),
         ("dense_eig", ctypes.c_int32),
+        ("basis", ctypes.c_int32),
+        ("explicit_rr", ctypes.c_int32),
+        ("criterion", ctypes.c_int32),
+        ("gram_blocks", ctypes.c_int32),
     ]
 
 
@@ -93,6 +98,7 @@ class lobpcg_stats_t(ctypes.Structure):
         ("eig_check_orthogonality", ctypes.c_int64),
         ("eig_check_wide_cluster", ctypes.c_int64),
         ("eig_check_nonfinite", ctypes.c_int64),
+        ("explicit_rr_calls", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -148,6 +154,9 @@ def load(build_if_missing=False):
         "lobpcg_syev": (I32, [I64, P, I64, P, I32, P]),
         "lobpcg_eig_adjoint": (I32, [P, I64, P, P, I64, P, P, I64, I32, P, P, I32, D, I32,
                                      ctypes.POINTER(I64)]),
+        "lobpcg_chebyshev_create": (I32, [ctypes.POINTER(P), I64, P, P, P, P, I32, D, D, I64]),
+        "lobpcg_chebyshev_apply": (I32, [P, I64, I64, P, I64, P, I64, P]),
+        "lobpcg_chebyshev_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +221,29 @@ def lobpcg_set_precond_diag(h, kdiag, mem=LOBPCG_MEM_HOST):
 
 def lobpcg_set_precond_callback(h, fn, ctx=None):
     return load().lobpcg_set_precond_callback(h, fn, ctx)
+
+
+def lobpcg_chebyshev_create(n, rowptr, col, val, diag, degree, lmin, lmax, max_cols):
+    c = P()
+    rc = load().lobpcg_chebyshev_create(ctypes.byref(c), n, ptr(rowptr), ptr(col), ptr(val),
+                                        ptr(diag), degree, lmin, lmax, max_cols)
+    check(rc, "lobpcg_chebyshev_create")
+    return c
+
+
+def lobpcg_chebyshev_apply(ctx, n, ncols, R, ldr, W, ldw, stream=None):
+    return load().lobpcg_chebyshev_apply(ctx, n, ncols, ptr(R), ldr, ptr(W), ldw,
+                                         stream_ptr(stream))
+
+
+def lobpcg_chebyshev_destroy(c):
+    load().lobpcg_chebyshev_destroy(c)
+
+
+def chebyshev_callback():
+    """lobpcg_chebyshev_apply as a callback pointer (called by the library
+    itself, no Python on the path)."""
+    return ctypes.cast(load().lobpcg_chebyshev_apply, PRECOND_FN)
 
 
 def lobpcg_solve(h, k, tol, X0, ldx0, seed, mem_in, lam, X, ldx, mem_out, resnorm=None):

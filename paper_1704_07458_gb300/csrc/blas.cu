@@ -214,7 +214,7 @@ int64_t residual_workspace(int64_t n, int m) {
 __global__ void __launch_bounds__(256) residual_kernel(
     int64_t n, const double* __restrict__ X, const double* __restrict__ AX,
     const double* __restrict__ BX, int64_t ld, int m, int c0, const double* __restrict__ theta,
-    const double* __restrict__ kinv, double* __restrict__ W, int64_t ldw,
+    const double* __restrict__ kinv, double* __restrict__ W, int64_t ldw, int xb,
     double* __restrict__ partial) {
   __shared__ double red[2][8][33];
   const int mm = m - c0;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) residual_kernel(
         const double bx = BX ? BX[o] : x;
         const double res = fma(-th, bx, AX[o]);
         rn = fma(res, res, rn);
-        xn = fma(x, x, xn);
+        xn = fma(x, xb ? bx : x, xn);  // ||x||^2, or x^T B x for criterion (8)
         if (W) W[r * ldw + (j - c0)] = kinv ? res * kinv[r] : res;
       }
     }
@@ -268,11 +268,11 @@ __global__ void residual_finish_kernel(const double* __restrict__ partial, int b
 
 int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, const double* BX,
              int64_t ld, int m, int c0, const double* theta, const double* kinv, double* W,
-             int64_t ldw, double normA, double normB, double* be, void* partial) {
+             int64_t ldw, double normA, double normB, double* be, void* partial, int xb) {
   const int mm = m - c0;
   if (mm <= 0) return LOBPCG_OK;
   const int blocks = row_blocks(n);
-  residual_kernel<<<blocks, 256, 0, st>>>(n, X, AX, BX, ld, m, c0, theta, kinv, W, ldw,
+  residual_kernel<<<blocks, 256, 0, st>>>(n, X, AX, BX, ld, m, c0, theta, kinv, W, ldw, xb,
                                           (double*)partial);
   LOB_LAUNCHED();
   residual_finish_kernel<<<(unsigned)ceil_div(mm, 128), 128, 0, st>>>(

@@ -47,6 +47,12 @@ __global__ void set_identity_kernel(int n, double* A, int lda) {
   A[i + (int64_t)j * lda] = i == j ? 1.0 : 0.0;
 }
 
+__global__ void set_zero_kernel(int rows, int cols, double* D, int ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * cols) return;
+  D[(e % rows) + (e / rows) * (int64_t)ldd] = 0.0;
+}
+
 __global__ void copy_mat_kernel(int rows, int cols, const double* S, int lds, double* D,
                                 int ldd) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,25 +78,32 @@ __global__ void svqb_t_kernel(int nu, int first, int nkeep, const double* d, con
   T[i + (int64_t)t * ldt] = d[i] * Z[i + (int64_t)(first + t) * ldz] / sqrt(th);
 }
 
-__global__ void assemble_kernel(int nx, int np, int nw, const double* theta, const double* PAP,
-                                int ldpap, const double* GAw, const double* GBw, int ldgw,
-                                double* SAS, double* SBS) {
+// Projected pencil on S = [X, P, W] (ns = nx + np + nw): the columns from c0
+// on come from Grams S^T (A S)(:, c0:) in GAw and S^T (B S)(:, c0:) in GBw
+// (GBw == nullptr: S^T B S = I there), mirrored below the diagonal and
+// symmetrised where both indices are >= c0; the rest from the identities
+// (12)-(14): X^T A X = Theta, X^T B X = I, X^T A P = X^T B P = 0, P^T B P = I,
+// P^T A P from Eq. (14).  c0 = nx + np: only the W columns are computed (the
+// method's own pencil); c0 = nx or 0: the comparison variants and the
+// explicit Rayleigh-Ritz.
+__global__ void assemble_kernel(int nx, int np, int nw, int c0, const double* theta,
+                                const double* PAP, int ldpap, const double* GAw,
+                                const double* GBw, int ldgw, double* SAS, double* SBS) {
   const int ns = nx + np + nw;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ns * ns) return;
   const int i = (int)(e % ns), j = (int)(e / ns);
-  const int o = nx + np;
   double a = 0.0, b = (i == j) ? 1.0 : 0.0;
-  if (j >= o) {
-    a = GAw[i + (int64_t)(j - o) * ldgw];
-    if (GBw) b = GBw[i + (int64_t)(j - o) * ldgw];
-    if (i >= o) {  // W^T A W block: symmetrise
-      a = 0.5 * (a + GAw[j + (int64_t)(i - o) * ldgw]);
-      if (GBw) b = 0.5 * (b + GBw[j + (int64_t)(i - o) * ldgw]);
+  if (j >= c0) {
+    a = GAw[i + (int64_t)(j - c0) * ldgw];
+    if (GBw) b = GBw[i + (int64_t)(j - c0) * ldgw];
+    if (i >= c0) {  // both computed: symmetrise
+      a = 0.5 * (a + GAw[j + (int64_t)(i - c0) * ldgw]);
+      if (GBw) b = 0.5 * (b + GBw[j + (int64_t)(i - c0) * ldgw]);
     }
-  } else if (i >= o) {
-    a = GAw[j + (int64_t)(i - o) * ldgw];
-    if (GBw) b = GBw[j + (int64_t)(i - o) * ldgw];
+  } else if (i >= c0) {
+    a = GAw[j + (int64_t)(i - c0) * ldgw];
+    if (GBw) b = GBw[j + (int64_t)(i - c0) * ldgw];
   } else if (i < nx && j < nx) {
     a = (i == j) ? theta[i] : 0.0;
   } else if (i >= nx && j >= nx) {
@@ -795,9 +808,11 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
 
 int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
                 int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
-                int* npn_out, double* theta, double* PAP) {
-  if (dev_rr_fits(L, ns, nx, use_ortho ? 0 : ns - nx - np))
-    return rr_modified_dev(L, SAS, SBS, ns, nx, np, nc, use_ortho, tau_skip, flip, condR, C,
+                int* npn_out, double* theta, double* PAP, bool structured) {
+  // the device path with o = 0 treats S^T B S as one dense block
+  const int o = structured ? nx + np : 0;
+  if (dev_rr_fits(L, ns, nx, use_ortho ? 0 : ns - o))
+    return rr_modified_dev(L, SAS, SBS, ns, nx, o - nx, nc, use_ortho, tau_skip, flip, condR, C,
                            npn_out, theta, PAP);
   *flip = false;
   *condR = 1.0;
@@ -894,6 +909,76 @@ int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int
   return LOBPCG_OK;
 }
 
+// C = alpha op(A) op(B) + beta C (column-major): this library's kernels for
+// the sizes its device path takes, cuBLAS above them
+static int small_gemm(DenseLayer& L, bool ta, bool tb, int m, int n, int k, double alpha,
+                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                      int ldc) {
+  if (m <= 0 || n <= 0) return LOBPCG_OK;
+  if (L.eig_mode == 0 && m <= L.dev.nmax && n <= 2 * L.dev.nmax)
+    return dev_gemm(L, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, nullptr);
+  BLAS_OK(cublasDgemm(L.blas, ta ? CUBLAS_OP_T : CUBLAS_OP_N, tb ? CUBLAS_OP_T : CUBLAS_OP_N, m,
+                      n, k, &alpha, A, lda, B, ldb, &beta, C, ldc));
+  return LOBPCG_OK;
+}
+
+int rr_hl(DenseLayer& L, const double* SAS, int ns, int nx, int nc, double* C, int* npn_out,
+          double* theta, double* PAP) {
+  double* Z = L.A[3];
+  double* Y = L.A[4];
+  double* T1 = L.A[5];
+  double* Tq = L.A[2];
+  int rc;
+  // eigenpairs of S^T A S into Z, L.ev
+  if (dev_rr_fits(L, ns, 0, 0)) {
+    int* est = L.dev.ints + 2;
+    ++L.dev_calls;
+    if ((rc = dev_syev(L, ns, SAS, ns, Z, ns, L.ev, est))) return rc;
+    int fl = 0;
+    if ((rc = to_host(L, L.host, est, sizeof(int)))) return rc;
+    memcpy(&fl, L.host, sizeof(int));
+    if (fl != 0) {
+      if ((rc = copy_mat(L, ns, ns, SAS, ns, Z, ns))) return rc;
+      if ((rc = syevd_fallback(L, ns, Z, ns))) return rc;
+    }
+  } else {
+    if ((rc = copy_mat(L, ns, ns, SAS, ns, Z, ns))) return rc;
+    if ((rc = syevd(L, true, ns, Z, ns))) return rc;
+  }
+  if ((rc = copy_mat(L, ns, nx, Z, ns, C, ns))) return rc;  // C_x = Z_x
+  // Theta now: the svqb below reuses the eigenvalue buffer
+  LOB_CUDA_OK(cudaMemcpyAsync(theta, L.ev, nx * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+  const int nu = nx - nc;
+  int keep = 0;
+  if (nu > 0 && ns > nx) {
+    // Y = [0; Z_2(:, nc:nx)] - Z_x (Z_x^T [0; Z_2(:, nc:nx)])
+    set_zero_kernel<<<blocks_for((int64_t)ns * nu), 256, 0, L.st>>>(ns, nu, Y, ns);
+    LAUNCH_OK(L);
+    if ((rc = copy_mat(L, ns - nx, nu, Z + nx + (int64_t)nc * ns, ns, Y + nx, ns))) return rc;
+    if ((rc = small_gemm(L, true, false, nx, nu, ns - nx, 1.0, Z + nx, ns, Z + nx + (int64_t)nc * ns,
+                         ns, 0.0, T1, nx)))
+      return rc;
+    if ((rc = small_gemm(L, false, false, ns, nu, nx, -1.0, Z, ns, T1, nx, 1.0, Y, ns))) return rc;
+    // svqb (Algorithm 4, Euclidean metric): G = Y^T Y, T = D Z_G Theta^-1/2, C_p = Y T
+    if ((rc = small_gemm(L, true, false, nu, nu, ns, 1.0, Y, ns, Y, ns, 0.0, T1, nu))) return rc;
+    if ((rc = svqb_transform(L, T1, nu, false, nu * kEps, Tq, &keep))) return rc;
+    if (keep > 0) {
+      if ((rc = small_gemm(L, false, false, ns, keep, nu, 1.0, Y, ns, Tq, nu, 0.0,
+                           C + (int64_t)nx * ns, ns)))
+        return rc;
+      // P^T A P = C_p^T (S^T A S) C_p
+      if ((rc = small_gemm(L, false, false, ns, keep, ns, 1.0, SAS, ns, C + (int64_t)nx * ns, ns,
+                           0.0, Y, ns)))
+        return rc;
+      if ((rc = small_gemm(L, true, false, keep, keep, ns, 1.0, C + (int64_t)nx * ns, ns, Y, ns,
+                           0.0, PAP, keep)))
+        return rc;
+    }
+  }
+  *npn_out = keep;
+  return LOBPCG_OK;
+}
+
 int svqb_transform(DenseLayer& L, const double* G, int nu, bool drop, double tau, double* T,
                    int* nkeep) {
   *nkeep = 0;
@@ -928,9 +1013,10 @@ int svqb_transform(DenseLayer& L, const double* G, int nu, bool drop, double tau
 
 int assemble(DenseLayer& L, int nx, int np, int nw, const double* theta, const double* PAP,
              int ldpap, const double* GAw, const double* GBw, int ldgw, double* SAS,
-             double* SBS) {
+             double* SBS, int c0) {
   const int ns = nx + np + nw;
-  assemble_kernel<<<blocks_for((int64_t)ns * ns), 256, 0, L.st>>>(nx, np, nw, theta, PAP,
+  if (c0 < 0) c0 = nx + np;
+  assemble_kernel<<<blocks_for((int64_t)ns * ns), 256, 0, L.st>>>(nx, np, nw, c0, theta, PAP,
                                                                   std::max(ldpap, 1), GAw, GBw,
                                                                   ldgw, SAS, SBS);
   LAUNCH_OK(L);

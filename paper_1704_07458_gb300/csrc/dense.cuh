@@ -82,11 +82,21 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
 // writes C = [C_x, C_p] (ns x (nx + *npn), leading dim ns), theta (device, nx)
 // and PAP (npn x npn, leading dim npn).  *flip reports the switch to the
 // orthogonal branch (Cholesky failure or cond(R)^-3 < tau_skip).
-// np: columns of P in S = [X, P, W] (the identities (12)-(13) make S^T B S
-// the identity outside the W columns, which the device path uses).
+// np: columns of P in S = [X, P, W].  structured: S^T B S came from the
+// identities (12)-(13) and is the identity outside the W columns, which the
+// device path uses (only the W-block Schur complement is factored); false
+// when every block was computed explicitly.
 int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
                 int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
-                int* npn, double* theta, double* PAP);
+                int* npn, double* theta, double* PAP, bool structured = true);
+
+// Rayleigh-Ritz of the Hetmaniuk-Lehoucq basis selection (the comparison
+// variants of Sec. 6): S is B-orthonormal, eig(S^T A S) = Z Theta Z^T,
+// C_x = Z(:, 0:nx), C_p = the svqb orthonormalisation (Algorithm 4) of
+// [0; Z_2(:, nc:nx)] - Z_x Z_x^T [0; Z_2(:, nc:nx)] (Eq. 6), P^T A P =
+// C_p^T S^T A S C_p.  Same outputs as rr_modified.
+int rr_hl(DenseLayer& L, const double* SAS, int ns, int nx, int nc, double* C, int* npn,
+          double* theta, double* PAP);
 
 // svqb (drop == false, Algorithm 4) or svqbDrop (drop == true, Algorithm 6) on
 // the Gram G = U^T B U (nu x nu, leading dim nu): T = D Z(:, J) Theta(J)^-1/2,
@@ -97,9 +107,12 @@ int svqb_transform(DenseLayer& L, const double* G, int nu, bool drop, double tau
 // Assemble the projected pencil on S = [X, P, W] from Theta, the saved P^T A P
 // (Eq. 14), the identities (12)-(13) and the W columns GAw = S^T A W,
 // GBw = S^T B W (ns x nw, leading dim ldgw; GBw == nullptr: S^T B S = I).
+// c0 (default nx + np, the W columns): first column of S^T A S, S^T B S that
+// GAw, GBw hold (ns x (ns - c0)); the blocks left of and above c0 come from
+// the identities.
 int assemble(DenseLayer& L, int nx, int np, int nw, const double* theta, const double* PAP,
              int ldpap, const double* GAw, const double* GBw, int ldgw, double* SAS,
-             double* SBS);
+             double* SBS, int c0 = -1);
 
 // out[0] = ||G - I||_F (identity == true) or ||G||_F; out[1] = sum(a[0:na]);
 // out[2] = sum(b[0:nb]).  G: rows x cols, leading dim ldg.  Result to host.

@@ -61,9 +61,11 @@ int64_t update_ozaki_workspace(int64_t n, int s, int m, int slices);
 // preconditioner enters as its reciprocal diagonal kinv (nullptr: K = I).
 // partial: device scratch of residual_workspace(n, m) bytes.
 int64_t residual_workspace(int64_t n, int m);
+// xb != 0: the column norm in the denominator is sqrt(x^T B x) instead of
+// ||x|| (criterion (8) of Sec. 4.3, with normA = 0 and normB = 1).
 int residual(cudaStream_t st, int64_t n, const double* X, const double* AX, const double* BX,
              int64_t ld, int m, int c0, const double* theta, const double* kinv, double* W,
-             int64_t ldw, double normA, double normB, double* be, void* partial);
+             int64_t ldw, double normA, double normB, double* be, void* partial, int xb = 0);
 // out = 1 / d (n values)
 int reciprocal(cudaStream_t st, int64_t n, const double* d, double* out);
 

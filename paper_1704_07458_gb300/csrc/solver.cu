@@ -374,8 +374,10 @@ int64_t leading_converged(const double* be, int64_t m, double tol) {
 // Algorithm 5 (orthoDrop) with M = B on the active W columns.  U points at the
 // active block (inside one of the wbuf buffers); the result may move to another
 // buffer.  V = [X, P] with BV = [BX, BP].
+// drop == false: Algorithm 3 (svqb on every inner pass, no column dropped),
+// the orthogonalisation of the Hetmaniuk-Lehoucq comparison variants.
 int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int np,
-               double tau_ortho) {
+               double tau_ortho, bool drop = true) {
   Scoped sc(h->timer, PH_ORTHO);
   h->stats.ortho_calls++;
   const int nin = nu;
@@ -422,7 +424,8 @@ int ortho_drop(lobpcg_ctx* h, double*& U, double*& Ubase, int& nu, int nx, int n
       int keep = 0;
       {
         Scoped sd(h->timer, PH_DENSE);
-        if ((rc = svqb_transform(h->dense, h->Gs, nu, j > 0, nu * kEps, h->Cm, &keep))) return rc;
+        if ((rc = svqb_transform(h->dense, h->Gs, nu, drop && j > 0, nu * kEps, h->Cm, &keep)))
+          return rc;
       }
       h->stats.svqb_passes++;
       if (keep == 0) {
@@ -505,6 +508,16 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   bool implicit = h->b_kind == 0 || (h->b_kind == 1 && h->b_cond <= 1e4);
   if (h->opt.implicit == 1) implicit = false;
   if (h->opt.implicit == 2) implicit = true;
+  // basis selection: Algorithm 8, or the Hetmaniuk-Lehoucq comparison
+  // variants of Sec. 6 (CHL: no implicit products, every block computed;
+  // AHL: implicit products, only (12) assumed)
+  const int basis = (h->opt.basis == 1 || h->opt.basis == 2) ? h->opt.basis : 0;
+  const bool hl = basis != 0;
+  if (basis == 1) implicit = false;
+  // explicit Rayleigh-Ritz after refreshes: default on in the emulated forms
+  const bool erx = h->opt.explicit_rr == 2 || (h->opt.explicit_rr == 0 && gemm_mode(h) != 0);
+  // convergence test: Eq. (9), or the relative residuals (7) / (8)
+  const int crit = (h->opt.criterion == 7 || h->opt.criterion == 8) ? h->opt.criterion : 9;
   const double* kd = (h->k_kind == 0) ? h->adiag : (h->k_kind == 1 ? h->kdiag : nullptr);
   if (kd) {
     if ((rc = reciprocal(h->st, n, kd, h->kinv))) return rc;
@@ -568,7 +581,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
 
   int64_t nc = 0;
   int np = 0;
-  bool use_ortho = false, refresh_next = false;
+  bool use_ortho = hl, refresh_next = false, explicit_next = false;
   constexpr int64_t kStallWindow = 400;
   int64_t stall_nc = -1, stall_it = 0;
   double stall_be = INFINITY;
@@ -577,13 +590,17 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   // W (or R for a callback preconditioner) of columns c0 .. nx-1, then locking.
   double* Wbase = h->wbuf[0];
   double* Wp = Wbase;
+  // criterion (9): ||r|| / ((||A|| + |theta| ||B||) ||x||); (7): ||r|| /
+  // (|theta| ||x||); (8): ||r|| / (|theta| ||x||_B)
+  const double cA = crit == 9 ? normA : 0.0, cB = crit == 9 ? normB : 1.0;
   auto residual_step = [&](int64_t c0, bool write_w) -> int {
     Scoped sc(h->timer, PH_RESID);
     const double* bx = h->b_kind ? h->BX : nullptr;
     double* dst = nullptr;
     if (write_w) dst = (h->k_kind == 3) ? h->wbuf[3] : Wbase;
     int r = residual(h->st, n, h->X, h->AX, bx, ld, (int)nx, (int)c0, h->theta,
-                     (h->k_kind == 3) ? nullptr : kd, dst, ld, normA, normB, h->be, h->rwork);
+                     (h->k_kind == 3) ? nullptr : kd, dst, ld, cA, cB, h->be, h->rwork,
+                     crit == 8 ? 1 : 0);
     return r;
   };
   auto finish_w = [&](int64_t c0, int64_t ncn) -> int {
@@ -619,9 +636,14 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
       }
       ++it;
       int nw = (int)(nx - nc);
-      const bool need_sbs = true;
-      // W-products, Gram of the W columns, projected pencil, Algorithm 7
-      auto project = [&](bool ortho, double* SASo, double* SBSo) -> int {
+      // which blocks of the projected pencil are computed rather than taken
+      // from the identities (12)-(14): the W columns (Algorithm 8), P and W
+      // (AHL), or all (CHL, and the explicit Rayleigh-Ritz after a refresh)
+      const bool direct_all =
+          basis == 1 || (explicit_next && !hl) || (basis == 0 && h->opt.gram_blocks == 2);
+      if (explicit_next && !hl) h->stats.explicit_rr_calls++;
+      // W-products, Grams, projected pencil
+      auto project = [&](bool ortho, int c0, bool need_b) -> int {
         int r;
         double* BWp = h->b_kind ? h->BW : Wp;
         if ((r = apply_AB(h, Wp, nw, h->AW, h->b_kind ? h->BW : nullptr))) return r;
@@ -630,48 +652,82 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
         seg_push(S, h->X, ld, (int)nx);
         seg_push(S, h->P, ld, np);
         seg_push(S, Wp, ld, nw);
-        SegList V = seg_empty();
-        seg_push(V, h->AW, ld, nw);
-        if (!ortho && need_sbs) seg_push(V, BWp, ld, nw);
+        const double* BXp = h->b_kind ? h->BX : h->X;
+        const double* BPp = h->b_kind ? h->BP : h->P;
+        SegList VA = seg_empty(), VB = seg_empty();
+        if (c0 <= 0) {
+          seg_push(VA, h->AX, ld, (int)nx);
+          seg_push(VB, BXp, ld, (int)nx);
+        }
+        if (c0 <= (int)nx) {
+          seg_push(VA, h->AP, ld, np);
+          seg_push(VB, BPp, ld, np);
+        }
+        seg_push(VA, h->AW, ld, nw);
+        seg_push(VB, BWp, ld, nw);
+        const int nd = ns - c0;  // computed columns
+        const bool with_b = need_b && !ortho;
         {
           Scoped sc(h->timer, PH_GRAM);
-          if ((r = gram(h, S, V, h->Gw, ns))) return r;
+          if (c0 == (int)nx + np) {  // one Gram for S^T [A W, B W]
+            SegList V = VA;
+            if (with_b) seg_push(V, BWp, ld, nw);
+            if ((r = gram(h, S, V, h->Gw, ns))) return r;
+          } else {
+            if ((r = gram(h, S, VA, h->Gw, ns))) return r;
+            if (with_b && (r = gram(h, S, VB, h->Gw + (int64_t)ns * nd, ns))) return r;
+          }
         }
         Scoped sd(h->timer, PH_DENSE);
         return assemble(h->dense, (int)nx, np, nw, h->theta, h->PAP, np, h->Gw,
-                        ortho ? nullptr : h->Gw + (int64_t)ns * nw, ns, SASo, SBSo);
+                        with_b ? h->Gw + (int64_t)ns * nd : nullptr, ns, h->SAS, h->SBS, c0);
       };
+      const bool p_direct = basis == 2 || (basis == 0 && h->opt.gram_blocks == 1);
+      const int c0 = direct_all ? 0 : (p_direct ? (int)nx : (int)nx + np);
       if (use_ortho) {
-        if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
+        if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho, !hl))) return rc;
       }
-      if ((rc = project(use_ortho, h->SAS, h->SBS))) return rc;
+      // the explicit Rayleigh-Ritz runs the Cholesky branch on the computed
+      // S^T B S even after the switch to orthogonalisation
+      const bool chol_branch = !hl && (!use_ortho || direct_all);
+      if ((rc = project(!chol_branch, c0, !hl))) return rc;
       int ns = (int)nx + np + nw;
       bool flip = false;
       double condR = 1.0;
       int npn = 0;
       {
         Scoped sd(h->timer, PH_DENSE);
-        if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, np, (int)nc, use_ortho, tau_skip,
-                              &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
-          return rc;
+        if (hl) {
+          rc = rr_hl(h->dense, h->SAS, ns, (int)nx, (int)nc, h->Cm, &npn, h->theta, h->PAPn);
+        } else {
+          rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, np, (int)nc, !chol_branch,
+                           tau_skip, &flip, &condR, h->Cm, &npn, h->theta, h->PAPn,
+                           c0 == (int)nx + np);
+        }
+        if (rc) return rc;
       }
+      bool chol_used = chol_branch && !flip;
       if (flip) {
-        // Algorithm 8: switch to orthogonalisation, redo basis selection and projection
-        use_ortho = true;
-        h->stats.flip_iteration = it;
-        if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
-        if ((rc = project(true, h->SAS, h->SBS))) return rc;
-        ns = (int)nx + np + nw;
         Scoped sd(h->timer, PH_DENSE);
+        if (!use_ortho) {
+          // Algorithm 8: switch to orthogonalisation, redo basis selection and projection
+          use_ortho = true;
+          h->stats.flip_iteration = it;
+          if ((rc = ortho_drop(h, Wp, Wbase, nw, (int)nx, np, tau_ortho))) return rc;
+          if ((rc = project(true, c0, false))) return rc;
+          ns = (int)nx + np + nw;
+        }
         if ((rc = rr_modified(h->dense, h->SAS, h->SBS, ns, (int)nx, np, (int)nc, true, tau_skip,
-                              &flip, &condR, h->Cm, &npn, h->theta, h->PAPn)))
+                              &flip, &condR, h->Cm, &npn, h->theta, h->PAPn, c0 == (int)nx + np)))
           return rc;
+        chol_used = false;
       }
       // Algorithm 8 update and Sec. 5.2: [X, P] = S [C_x, C_p] (+ implicit products)
       const int mo = (int)nx + npn;
       const bool refresh = refresh_next || (it % refresh_every == 0);
+      explicit_next = erx && refresh && !hl;
       const int* bal = h->zexp;
-      if (!use_ortho) {
+      if (chol_used) {
         if ((rc = diag_exponents(h->st, ns, h->SBS, ns, h->cexp))) return rc;
         bal = h->cexp;
       }

@@ -376,3 +376,112 @@ def test_csr_metric_closed_form_and_brute_force():
     np.testing.assert_allclose(r.lam, synth.closed_form_mass_pencil(N, c, k), rtol=1e-9)
     Bd = B.to_dense()
     np.testing.assert_allclose(r.X.T @ Bd @ r.X, np.eye(k), atol=1e-12)
+
+
+# ---------------------------------------------------- HL comparison variants
+
+def test_ortho_algorithm3_contract():
+    """Algorithm 3: the output is B-orthonormal, B-orthogonal to V, and keeps
+    every column (svqb replaces small singular values instead of dropping)."""
+    rng = np.random.default_rng(4)
+    n = 150
+    b = _rand_metric(n, rng)
+    V = rng.standard_normal((n, 5))
+    V, _ = L.ortho(lambda Y: b[:, None] * Y, V, np.zeros((n, 0)), np.zeros((n, 0)), 100 * L.EPS)
+    U = rng.standard_normal((n, 7))
+    U[:, 6] = U[:, 0] + 1e-9 * U[:, 1]  # nearly dependent column
+    Uo, BUo = L.ortho(lambda Y: b[:, None] * Y, U, V, b[:, None] * V, 100 * L.EPS)
+    assert Uo.shape[1] == 7
+    np.testing.assert_allclose(Uo.T @ BUo, np.eye(7), atol=1e-10)
+    np.testing.assert_allclose(V.T @ (b[:, None] * Uo), 0.0, atol=1e-12)
+
+
+def test_rayleigh_ritz_hl_cp_is_orthonormal_and_orthogonal_to_cx():
+    rng = np.random.default_rng(5)
+    ns, nx, nc = 24, 8, 2
+    M = rng.standard_normal((ns, ns))
+    SAS = M @ M.T
+    rr = L.rayleigh_ritz_hl(SAS, nx, nc)
+    C = np.hstack([rr.Cx, rr.Cp])
+    np.testing.assert_allclose(C.T @ C, np.eye(C.shape[1]), atol=1e-12)
+    np.testing.assert_allclose(rr.Cx.T @ SAS @ rr.Cx, np.diag(rr.theta), atol=1e-10)
+    np.testing.assert_allclose(rr.PAP, rr.Cp.T @ SAS @ rr.Cp, atol=1e-12)
+    assert rr.Cp.shape[1] == nx - nc
+
+
+@pytest.mark.parametrize("basis", ["chl", "ahl"])
+def test_hl_variants_reach_the_closed_form_on_c1(basis):
+    p = synth.make_problem("lap2d_32")
+    _, r = _run(p, opts=L.Options(basis=basis))
+    assert r.status == L.OK
+    np.testing.assert_allclose(r.lam, p.closed_form[:p.k], rtol=1e-10)
+    assert r.stats["ortho_calls"] == r.iters  # HL orthogonalises W on every iteration
+
+
+@pytest.mark.parametrize("basis", ["chl", "ahl"])
+def test_hl_variants_agree_with_algorithm8_generalised(basis):
+    p = synth.make_problem("lap3d_64_diagB", N=8, k=6)
+    _, r8 = _run(p)
+    _, rh = _run(p, opts=L.Options(basis=basis))
+    assert rh.status == L.OK
+    np.testing.assert_allclose(rh.lam, r8.lam, rtol=1e-10)
+
+
+# ---------------------------------------------------- Chebyshev preconditioner
+
+def _spd_with_spectrum(n, w, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q @ np.diag(w) @ Q.T
+
+
+def test_chebyshev_precond_degree_one_is_scaled_jacobi():
+    import scipy.sparse as sp_
+    A = sp_.csr_matrix(_spd_with_spectrum(20, np.linspace(1, 3, 20), 1) + 5 * np.eye(20))
+    R = np.random.default_rng(2).standard_normal((20, 3))
+    K = L.chebyshev_precond(A, 1, 0.5, 2.5)
+    np.testing.assert_allclose(K(R), R / A.diagonal()[:, None] / 1.5, rtol=1e-15)
+
+
+def test_chebyshev_precond_error_bound_and_symmetry():
+    """For D = I (unit diagonal) and the spectrum inside [lmin, lmax], the
+    Chebyshev iteration's error after k steps is at most 2 q^k ||A^-1 r||_A
+    in the A-norm, q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1) (Saad, Eq.
+    12.14), and K^-1 = p(A) is symmetric."""
+    import scipy.sparse as sp_
+    n = 40
+    w = np.linspace(0.2, 1.8, n)
+    M = _spd_with_spectrum(n, w, 3)
+    d = np.sqrt(np.diag(M))
+    A = M / d[:, None] / d[None, :]          # unit diagonal, D^-1 A = A
+    lam = np.linalg.eigvalsh(A)
+    lmin, lmax = lam[0] * 0.999, lam[-1] * 1.001
+    Asp = sp_.csr_matrix(A)
+    r = np.random.default_rng(4).standard_normal((n, 1))
+    x = np.linalg.solve(A, r)
+    kappa = lmax / lmin
+    q = (np.sqrt(kappa) - 1) / (np.sqrt(kappa) + 1)
+    anorm = lambda v: float(np.sqrt((v.T @ A @ v).item()))
+    for k in (2, 5, 10, 20):
+        e = L.chebyshev_precond(Asp, k, lmin, lmax)(r) - x
+        assert anorm(e) <= 2 * q ** k * anorm(x) * (1 + 1e-10)
+    K = L.chebyshev_precond(Asp, 6, lmin, lmax)
+    Kmat = K(np.eye(n))
+    np.testing.assert_allclose(Kmat, Kmat.T, atol=1e-12)
+    assert np.linalg.eigvalsh(Kmat)[0] > 0
+
+
+def test_lobpcg_with_chebyshev_precond_converges_faster():
+    import scipy.sparse as sp_
+    p = synth.make_problem("lap2d_32")
+    A = sp_.csr_matrix((p.A.val, p.A.col, p.A.rowptr), shape=(p.n, p.n))
+    K = L.chebyshev_precond(A, 4, 0.05, 2.0)   # D^-1 A of the Laplacian lies in (0, 2)
+    pen = L.Pencil(p.n, (p.A.rowptr, p.A.col, p.A.val), None, None, k_fn=K)
+    nx = synth.block_width(p.k, p.n)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, nx)
+    Om = synth.normal_block(0, synth.STREAM_OMEGA, p.n, 16).T
+    r = L.lobpcg(pen, X0, p.k, p.tol, Om)
+    assert r.status == L.OK
+    np.testing.assert_allclose(r.lam, p.closed_form[:p.k], rtol=1e-10)
+    _, rj = _run(p)
+    assert r.iters < rj.iters
