@@ -222,13 +222,15 @@ int ensure_workspace(lobpcg_ctx* h, int64_t nx) {
   if ((rc = dalloc(h, (void**)&h->zexp, (size_t)nsmax * sizeof(int)))) return rc;
   if ((rc = dalloc(h, (void**)&h->dstatus, 16))) return rc;
   LOB_CUDA_OK(cudaMemsetAsync(h->zexp, 0, (size_t)nsmax * sizeof(int), h->st));
-  // Gram scratch: the widest use is S^T [AW, BW] (3 nx x 2 nx) or X^T [AX, BX].
+  // Gram scratch: the widest uses are S^T [AW, BW] (3 nx x 2 nx) and, when
+  // every block is computed (CHL, the explicit Rayleigh-Ritz), S^T A S and
+  // S^T B S (3 nx x 3 nx each).
   const int mode = gemm_mode(h), sl = slices(h);
   // The slab count depends on the shape, so take the maximum over every Gram
-  // shape the driver can request (p <= 3 n_x, q <= 2 n_x).
+  // shape the driver can request (p <= 3 n_x, q <= 3 n_x).
   int64_t gb = 0;
   for (int p = 1; p <= nsmax; ++p)
-    for (int q = 1; q <= 2 * nx; ++q) {
+    for (int q = 1; q <= nsmax; ++q) {
       gb = std::max(gb, gram_f64_workspace(n, p, q));
       if (mode) gb = std::max(gb, gram_ozaki_workspace(n, p, q, std::max(sl, 7)));
       if (mode == LOBPCG_GEMM_OZAKI_TC) gb = std::max(gb, gram_tc_workspace(n, p, q));

@@ -13,6 +13,16 @@
       one timed solve per arithmetic form (FP64, mma.sync emulation, tcgen05
       emulation with 7, 6, 5 slices): seconds, iterations, backward error and
       the largest relative eigenvalue difference from the FP64 form.
+  python -m paper_1704_07458_gb300.profiling versions [--workload ...] [--N 32 --k 32]
+      the component breakdown of the implementation versions of Sec. 6.2
+      (Fig. 2 methodology) on a synthetic workload: CHL, AHL, Algorithm 8's
+      basis selection with orthogonalisation on every iteration and only
+      identity (12), the same with orthogonalisation skipped while cond(R)
+      allows, and Algorithm 8; per version the time, iterations, per-phase
+      times, svqb passes per orthogonalisation call and the eigenvalue
+      difference from Algorithm 8.
+  python -m paper_1704_07458_gb300.profiling ksweep [--workload ...] [--ks 16,32,64,128]
+      time to k eigenpairs against k on one operator (Fig. 4 methodology).
 """
 import argparse
 import collections
@@ -180,6 +190,93 @@ def compare_forms(workload, forms):
         s.close()
 
 
+# (label, solver options) of the versions of Sec. 6.2, Fig. 2; the blockwise
+# basis update that separates versions 1/2 and 3/4 there is this library's
+# tiled update in every version
+VERSIONS = [
+    ("1-2 CHL", dict(basis=1)),
+    ("3-4 AHL", dict(basis=2)),
+    ("5 robust ortho every it, (12) only", dict(basis=0, gram_blocks=1, tau_skip=1.0)),
+    ("6 + skip ortho", dict(basis=0, gram_blocks=1)),
+    ("7 Algorithm 8", dict(basis=0)),
+]
+
+
+def _solve_once(p, opts, X0, warm=True):
+    """One timed solve (CUDA events on the solver's stream) -> (lam, stats dict)."""
+    import numpy as np
+    import torch
+    from . import Solver
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    st_ = torch.cuda.current_stream()
+    s = Solver(stream=st_, **opts)
+    s.set_operator(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val),
+                   b_diag=None if p.b_diag is None else dev(p.b_diag))
+    if warm:
+        s.solve(p.k, p.tol, X0=X0, device=True, raise_on_error=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st_)
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, device=True, raise_on_error=False)
+    e1.record(st_)
+    torch.cuda.synchronize()
+    st = s.stats()
+    s.close()
+    st["seconds"] = e0.elapsed_time(e1) / 1e3
+    st["status"] = rc
+    st["max_backward_error"] = float(be.max().item())
+    return lam.cpu().numpy(), st
+
+
+def versions(workload, mode, kw):
+    import numpy as np
+    import torch
+    import synth
+    p = synth.make_problem(workload, seed=0, **kw)
+    nx = synth.block_width(p.k, p.n)
+    X0 = torch.from_numpy(synth.normal_block(0, synth.STREAM_X0, p.n, nx)).cuda()
+    rows, ref = [], None
+    for label, opts in reversed(VERSIONS):
+        lam, st = _solve_once(p, dict(gemm_mode=mode, maxit=6000, **opts), X0)
+        if ref is None:
+            ref = lam
+        rows.append((label, st, float(np.max(np.abs(lam - ref) / np.abs(ref)))))
+    rows.reverse()
+    out = {"workload": workload, "n": p.n, "k": p.k, "mode": mode, "versions": []}
+    for label, st, dl in rows:
+        out["versions"].append({
+            "version": label, "status": st["status"], "seconds": st["seconds"],
+            "iterations": st["iterations"], "max_backward_error": st["max_backward_error"],
+            "ms": {k[3:]: st[k] for k in ("ms_spmm", "ms_gram", "ms_update", "ms_residual",
+                                          "ms_small_dense", "ms_ortho", "ms_other")},
+            "ortho_calls": st["ortho_calls"],
+            "svqb_passes_per_ortho_call": st["svqb_passes"] / max(1, st["ortho_calls"]),
+            "flip_iteration": st["flip_iteration"], "dropped_columns": st["dropped_columns"],
+            "max_rel_lambda_diff_vs_algorithm8": dl})
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def ksweep(workload, mode, ks, kw):
+    import torch
+    import synth
+    out = {"workload": workload, "mode": mode, "points": []}
+    for k in ks:
+        p = synth.make_problem(workload, seed=0, k=k, **kw)
+        nx = synth.block_width(p.k, p.n)
+        X0 = torch.from_numpy(synth.normal_block(0, synth.STREAM_X0, p.n, nx)).cuda()
+        lam, st = _solve_once(p, dict(gemm_mode=mode, maxit=6000), X0, warm=False)
+        out["points"].append({
+            "k": k, "n_x": nx, "status": st["status"], "seconds": st["seconds"],
+            "iterations": st["iterations"], "max_backward_error": st["max_backward_error"],
+            "ms_per_iteration": 1e3 * st["seconds"] / max(1, st["iterations"]),
+            "ms": {kk[3:]: st[kk] for kk in ("ms_spmm", "ms_gram", "ms_update", "ms_residual",
+                                             "ms_small_dense", "ms_ortho", "ms_other")}})
+        print(json.dumps(out["points"][-1]), flush=True)
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -196,7 +293,23 @@ def main(argv=None):
     l.add_argument("csv")
     f = sub.add_parser("forms")
     f.add_argument("--workload", default="lap3d_64_diagB")
+    v = sub.add_parser("versions")
+    v.add_argument("--workload", default="lap3d_64_diagB")
+    v.add_argument("--mode", default="f64", choices=["f64", "ozaki", "ozaki_tc"])
+    v.add_argument("--N", type=int, default=0)
+    v.add_argument("--k", type=int, default=0)
+    ks = sub.add_parser("ksweep")
+    ks.add_argument("--workload", default="lap3d_64_diagB")
+    ks.add_argument("--mode", default="ozaki_tc", choices=["f64", "ozaki", "ozaki_tc"])
+    ks.add_argument("--ks", default="16,32,64,128")
+    ks.add_argument("--N", type=int, default=0)
     a = ap.parse_args(argv)
+    if a.cmd == "versions":
+        kw = {kk: vv for kk, vv in (("N", a.N), ("k", a.k)) if vv}
+        return versions(a.workload, a.mode, kw)
+    if a.cmd == "ksweep":
+        kw = {"N": a.N} if a.N else {}
+        return ksweep(a.workload, a.mode, [int(x) for x in a.ks.split(",")], kw)
     if a.cmd == "launches":
         summarize_launches(a.csv)
     elif a.cmd == "forms":

@@ -65,8 +65,9 @@ def test_chebyshev_apply_entry_point_against_oracle():
     p = synth.make_problem("lap2d_32")
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     R = synth.normal_block(3, 1, p.n, 7)
-    c = gb.lobpcg_chebyshev_create(p.n, dev(p.A.rowptr), dev(p.A.col), dev(p.A.val), None, 5,
-                                   0.05, 2.0, 7)
+    # the object borrows the CSR arrays: they must stay alive while it is used
+    rp, ci, va = dev(p.A.rowptr), dev(p.A.col), dev(p.A.val)
+    c = gb.lobpcg_chebyshev_create(p.n, rp, ci, va, None, 5, 0.05, 2.0, 7)
     Rd = dev(R)
     Wd = torch.empty_like(Rd)
     rc = gb.lobpcg_chebyshev_apply(c, p.n, 7, Rd, 7, Wd, 7, None)
