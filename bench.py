@@ -261,7 +261,8 @@ def workload_config(args, p):
     return {"workload": f"{args.workload}: {p.note}, n={p.n}, nnz={p.A.nnz}, k={p.k}, "
                         f"tol={p.tol}", "n": p.n, "nnz": p.A.nnz, "k": p.k, "tol": p.tol,
             "block_width": None, "gemm_mode": args.mode,
-            "dense_eig": {0: "fp64_syevd", 1: "fp32_refined", 2: "device"}.get(
+            "dense_eig": {0: "device_layer_le256_else_fp64_syevd", 1: "fp32_syevd_refined",
+                          2: "fp64_syevd"}.get(
                 getattr(args, "dense_eig", 0), "?"),
             "ozaki_slices": getattr(args, "slices", 0) or 6,
             "l2": "working set > L2 (15 blocks of n x 72 doubles, 151 MB each); no flush",

@@ -65,7 +65,8 @@ typedef enum {
  * noted.  eps below is 2^-52. */
 typedef struct {
   int64_t block_width;    /* n_x; 0: k + max(ceil(k/10), 2), the paper's ~10 % padding (Sec. 6) */
-  int32_t maxit;          /* 0: 2000 iterations (Sec. 6) */
+  int32_t maxit;          /* 0: 6000 iterations (the paper stops its runs at 2000, Sec. 6; the
+                             512^2 Laplacian + V, k = 32, needs about 2100 in FP64 here) */
   int32_t implicit;       /* implicit product updates (Sec. 5.2): 0 auto (B = I or diagonal
                              B with cond <= 1e4), 1 never, 2 always */
   int32_t refresh_every;  /* 0: 50; explicit A X, A P recomputation period under implicit updates */
@@ -105,6 +106,11 @@ typedef struct {
                              computed (basis 0): 0 all of (12)-(14) (Algorithm 8); 1 only (12)
                              (X^T A X = Theta, X^T B X = I; the P blocks are computed); 2 none
                              (the versions study of Sec. 6.2) */
+  int32_t inject_wait_timeout_at; /* 0 off; i > 0: after the update of iteration i the solver
+                             sets bit 0 of its tensor-core status word itself, the bit a
+                             Gram or update kernel sets when one of its bounded waits runs
+                             out, so that tests follow that error path (LOBPCG_ERR_TIMEOUT,
+                             handle still usable) without a failing kernel */
 } lobpcg_options_t;
 
 /* Per-solve counters and phase times (Sec. 6.2 breakdown methodology). */
@@ -283,6 +289,14 @@ int64_t lobpcg_gram_workspace(int64_t n, int64_t p, int64_t q, int mode, int sli
  * the caller.  Nothing in it needs to start at zero. */
 int lobpcg_gram_noalloc(int64_t n, const double* U, int64_t ldu, int64_t p, const double* V,
                         int64_t ldv, int64_t q, double* G, int64_t ldg, int slices, void* stream);
+
+/* Self-test of the bounded waits of the tensor-core kernels: one CTA waits,
+ * with the same bounded mbarrier wait limited to `polls` polls, on a barrier
+ * phase that nothing completes, and records the timeout in a status word the
+ * way the Gram and update kernels do.  Returns LOBPCG_ERR_TIMEOUT when the
+ * wait ran out and was reported (the expected outcome), LOBPCG_ERR_CUDA if the
+ * launch failed, LOBPCG_ERR_ARG for polls < 1.  Synchronises the stream. */
+int lobpcg_wait_selftest(int32_t polls, void* stream);
 
 /* Basis update Y = beta * Y0 + alpha * S C (Eq. 10-11): S n x s row-major, C
  * s x m column-major (leading dimension ldc), Y and Y0 n x m row-major (Y0 may

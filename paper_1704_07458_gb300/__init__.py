@@ -26,6 +26,7 @@ from ._native import (  # noqa: F401
     lobpcg_update, lobpcg_eig_adjoint, lobpcg_syev,
     lobpcg_residual, lobpcg_philox_normal, load, library_path,
     lobpcg_chebyshev_create, lobpcg_chebyshev_apply, lobpcg_chebyshev_destroy,
+    lobpcg_wait_selftest,
 )
 
 __all__ = [n for n in dir() if n.startswith("lobpcg_") or n.startswith("LOBPCG_")] + [

@@ -35,6 +35,7 @@ EXPORTED = [
     "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
     "lobpcg_eig_adjoint", "lobpcg_syev",
     "lobpcg_chebyshev_create", "lobpcg_chebyshev_apply", "lobpcg_chebyshev_destroy",
+    "lobpcg_wait_selftest",
 ]
 
 
@@ -56,6 +57,7 @@ class lobpcg_options_t(ctypes.Structure):
         ("explicit_rr", ctypes.c_int32),
         ("criterion", ctypes.c_int32),
         ("gram_blocks", ctypes.c_int32),
+        ("inject_wait_timeout_at", ctypes.c_int32),
     ]
 
 
@@ -157,6 +159,7 @@ def load(build_if_missing=False):
         "lobpcg_chebyshev_create": (I32, [ctypes.POINTER(P), I64, P, P, P, P, I32, D, D, I64]),
         "lobpcg_chebyshev_apply": (I32, [P, I64, I64, P, I64, P, I64, P]),
         "lobpcg_chebyshev_destroy": (None, [P]),
+        "lobpcg_wait_selftest": (I32, [I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +290,11 @@ def lobpcg_gram_noalloc(n, U, ldu, p, V, ldv, q, G, ldg, slices=0, stream=None):
     """G = U^T V without allocating (fixed in-library scratch; see lobpcg.h)."""
     return load().lobpcg_gram_noalloc(n, ptr(U), ldu, p, ptr(V), ldv, q, ptr(G), ldg, slices,
                                       stream_ptr(stream))
+
+
+def lobpcg_wait_selftest(polls, stream=None):
+    """Bounded-wait self-test (see lobpcg.h): LOBPCG_ERR_TIMEOUT when the wait ran out."""
+    return load().lobpcg_wait_selftest(polls, stream_ptr(stream))
 
 
 def lobpcg_update(n, S, lds, s, C, ldc, m, alpha, beta, Y0, ldy0, Y, ldy,

@@ -536,6 +536,21 @@ LOBPCG_EXPORT int lobpcg_gram(int64_t n, const double* U, int64_t ldu, int64_t p
   return rc;
 }
 
+LOBPCG_EXPORT int lobpcg_wait_selftest(int32_t polls, void* stream) {
+  if (polls < 1) return LOBPCG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return LOBPCG_ERR_OOM;
+  int h = 0;
+  bool ok = cudaMemsetAsync(d, 0, sizeof(int), st) == cudaSuccess &&
+            lob::wait_selftest(st, polls, d) == LOBPCG_OK &&
+            cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return LOBPCG_ERR_CUDA;
+  return (h & 1) ? LOBPCG_ERR_TIMEOUT : LOBPCG_OK;
+}
+
 LOBPCG_EXPORT int lobpcg_update(int64_t n, const double* S, int64_t lds, int64_t s,
                                 const double* C, int64_t ldc, int64_t m, double alpha,
                                 double beta, const double* Y0, int64_t ldy0, double* Y,

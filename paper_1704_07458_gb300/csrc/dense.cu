@@ -809,6 +809,11 @@ int rr_initial(DenseLayer& L, const double* GA, const double* GB, int nx, double
 int rr_modified(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
                 int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
                 int* npn_out, double* theta, double* PAP, bool structured) {
+  // the explicit pencil (nothing from the identities): the device path
+  // factors the X, P block first, then the Schur complement of the W block
+  if (!structured && !use_ortho && dev_explicit_fits(L, ns, nx, np))
+    return rr_explicit_dev(L, SAS, SBS, ns, nx, np, nc, tau_skip, flip, condR, C, npn_out, theta,
+                           PAP);
   // the device path with o = 0 treats S^T B S as one dense block
   const int o = structured ? nx + np : 0;
   if (dev_rr_fits(L, ns, nx, use_ortho ? 0 : ns - o))

@@ -137,6 +137,10 @@ int rr_initial_dev(DenseLayer& L, const double* GA, const double* GB, int nx, do
 int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
                     int nc, bool use_ortho, double tau_skip, bool* flip, double* condR, double* C,
                     int* npn, double* theta, double* PAP);
+bool dev_explicit_fits(const DenseLayer& L, int ns, int nx, int np);
+int rr_explicit_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
+                    int nc, double tau_skip, bool* flip, double* condR, double* C, int* npn,
+                    double* theta, double* PAP);
 int svqb_transform_dev(DenseLayer& L, const double* G, int nu, bool drop, double tau, double* T,
                        int* nkeep);
 // cuSOLVER FP64 eigendecomposition in place (A: eigenvectors, L.ev: eigenvalues)

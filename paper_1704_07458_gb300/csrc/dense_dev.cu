@@ -1134,6 +1134,44 @@ __global__ void dscale2_kernel(int n, const double* __restrict__ GB, int ldb,
         di * (0.5 * (GA[i + (int64_t)j * lda] + GA[j + (int64_t)i * lda])) * dj;
 }
 
+// The congruence T1^T M T1, T1 = blkdiag(Y11, I), of the scaled explicit
+// pencil (MB, MA), completed from the blocks the GEMMs wrote: SB' has the
+// identity on its leading o x o block, Fb = Y11^T MB[0:o, o:] above and its
+// transpose below the diagonal, MB on the trailing block; SA' has the GEMM's
+// leading block, Ka[:, o:] = Y11^T MA[0:o, o:] off the diagonal and MA on the
+// trailing block.  Both come out with both triangles.
+__global__ void pre_fill_kernel(int ns, int o, const double* __restrict__ MB,
+                                const double* __restrict__ MA, int ldm,
+                                const double* __restrict__ Ka, int ldk, double* __restrict__ SB,
+                                double* __restrict__ SA, int lds) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ns * ns) return;
+  const int i = (int)(e % ns), j = (int)(e / ns);
+  if (i < o && j < o) {  // SA' leading block comes from its GEMM
+    SB[i + (int64_t)j * lds] = i == j ? 1.0 : 0.0;
+  } else if (i < o) {    // SB' upper off-diagonal block comes from its GEMM
+    SA[i + (int64_t)j * lds] = Ka[i + (int64_t)j * ldk];
+  } else if (j < o) {
+    SB[i + (int64_t)j * lds] = SB[j + (int64_t)i * lds];
+    SA[i + (int64_t)j * lds] = Ka[j + (int64_t)i * ldk];
+  } else {
+    SB[i + (int64_t)j * lds] = MB[i + (int64_t)j * ldm];
+    SA[i + (int64_t)j * lds] = MA[i + (int64_t)j * ldm];
+  }
+}
+
+// C(i, j) = d_i (i < o ? Ct(i, j) : C(i, j)): the coefficients in the basis
+// S back from the congruence, C = D blkdiag(Y11, I) C'.
+__global__ void pre_back_kernel(int ns, int m, int o, const double* __restrict__ d,
+                                const double* __restrict__ Ct, int ldt, double* __restrict__ C,
+                                int ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ns * m) return;
+  const int i = (int)(e % ns), j = (int)(e / ns);
+  const double x = i < o ? Ct[i + (int64_t)j * ldt] : C[i + (int64_t)j * ldc];
+  C[i + (int64_t)j * ldc] = d[i] * x;
+}
+
 // H (ns x ns): H[0:o, 0:o] = MA[0:o, 0:o]; H[0:o, o:] = Qm[0:o, :] and its
 // transpose below; H[o:, o:] is written by a GEMM.
 __global__ void assemble_h_kernel(int ns, int o, const double* __restrict__ MA, int ldm,
@@ -1876,6 +1914,86 @@ int rr_modified_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns,
   }
   DLAUNCH(L);
   return rr_tail(L, TZ, Z, ns, nx, nc, C, npn_out, theta, PAP);
+}
+
+// The explicit Rayleigh-Ritz (every block of S^T A S and S^T B S computed,
+// nothing taken from the identities (12)-(14)), device path.  With the
+// scaling D = diag(S^T B S)^-1/2, MB = D S^T B S D and MA likewise, the
+// leading o x o block (the X and P columns, o = n_x + n_p) is factored on its
+// own, MB11 = R11^T R11, Y11 = R11^-1; the congruence T1 = blkdiag(Y11, I)
+// turns the pencil into one whose B-block is [[I, Fb], [Fb^T, MB22]], which
+// the structured path above factors (Cholesky of the Schur complement only).
+// Together the two steps are the Cholesky factor of MB, R = [[R11, R11 Fb],
+// [0, Rw]], so this is Algorithm 7 on the explicit pencil; the coefficients
+// come back as C = D T1 C'.  The cond(R) estimate that drives the switch to
+// orthogonalisation is that of the second factor: R11 is the factor of the
+// Gram matrix of the previous iteration's B-orthonormal X and P, within
+// rounding of the identity.  A failed R11 factorisation is a Cholesky
+// failure (*flip, cond = inf), as in Algorithm 7.
+bool dev_explicit_fits(const DenseLayer& L, int ns, int nx, int np) {
+  const int o = nx + np;
+  return o <= kCholMax && dev_rr_fits(L, ns, nx, ns - o);
+}
+
+int rr_explicit_dev(DenseLayer& L, const double* SAS, const double* SBS, int ns, int nx, int np,
+                    int nc, double tau_skip, bool* flip, double* condR, double* C, int* npn_out,
+                    double* theta, double* PAP) {
+  DevDense& D = L.dev;
+  *flip = false;
+  *condR = 1.0;
+  const int o = nx + np, nw = ns - o;
+  // L.R[] hold the FP32-refinement blocks of dense_eig 1, unused on this path
+  double* SB = L.R[0];   // ns x ns, T1^T MB T1
+  double* SA = L.R[1];   // ns x ns, T1^T MA T1
+  double* R11 = L.R[2];  // o x o, then kept as Y11 in Y
+  double* Y = L.R[3];    // o x o, Y11
+  double* d0 = L.R[4];   // ns
+  double* Ka = L.R[5];   // o x ns, Y11^T MA[0:o, :]; then Y11 C'[0:o, :]
+  double* MB = L.A[0];
+  double* MA = L.A[1];
+  int* info = D.ints + 4 * D.nmax + 16;
+  int rc;
+  dscale2_kernel<<<nblk((int64_t)ns * ns), 256, 0, L.st>>>(ns, SBS, ns, SAS, ns, d0, MB, MA, ns);
+  DLAUNCH(L);
+  copy_block_cm_kernel<<<nblk((int64_t)o * o), 256, 0, L.st>>>(o, o, MB, ns, R11, o, 1.0);
+  DLAUNCH(L);
+  LOB_CUDA_OK(cudaMemsetAsync(info, 0, sizeof(int), L.st));
+  if ((rc = dev_chol(L, o, R11, o, info))) return rc;
+  int fl = 0;
+  LOB_CUDA_OK(cudaMemcpyAsync(L.host, info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  LOB_CUDA_OK(cudaStreamSynchronize(L.st));
+  ++L.syncs;
+  memcpy(&fl, L.host, sizeof(int));
+  if (fl != 0) {
+    *flip = true;
+    *condR = INFINITY;
+    return LOBPCG_OK;
+  }
+  if ((rc = dev_trinv(L, o, R11, o, Y, o, nullptr))) return rc;
+  // Ka = Y11^T MA[0:o, :], SA'11 = Ka[:, 0:o] Y11, SB'12 = Y11^T MB[0:o, o:]
+  if ((rc = dev_gemm(L, true, false, o, ns, o, 1.0, Y, o, MA, ns, 0.0, nullptr, 0, Ka, o,
+                     nullptr)))
+    return rc;
+  if ((rc = dev_gemm(L, false, false, o, o, o, 1.0, Ka, o, Y, o, 0.0, nullptr, 0, SA, ns,
+                     nullptr)))
+    return rc;
+  if (nw > 0 && (rc = dev_gemm(L, true, false, o, nw, o, 1.0, Y, o, MB + (int64_t)o * ns, ns, 0.0,
+                               nullptr, 0, SB + (int64_t)o * ns, ns, nullptr)))
+    return rc;
+  pre_fill_kernel<<<nblk((int64_t)ns * ns), 256, 0, L.st>>>(ns, o, MB, MA, ns, Ka, o, SB, SA, ns);
+  DLAUNCH(L);
+  int npn = 0;
+  if ((rc = rr_modified_dev(L, SA, SB, ns, nx, np, nc, false, tau_skip, flip, condR, C, &npn,
+                            theta, PAP)))
+    return rc;
+  if (*flip) return LOBPCG_OK;
+  const int m = nx + npn;
+  if ((rc = dev_gemm(L, false, false, o, m, o, 1.0, Y, o, C, ns, 0.0, nullptr, 0, Ka, o, nullptr)))
+    return rc;
+  pre_back_kernel<<<nblk((int64_t)ns * m), 256, 0, L.st>>>(ns, m, o, d0, Ka, o, C, ns);
+  DLAUNCH(L);
+  *npn_out = npn;
+  return LOBPCG_OK;
 }
 
 // svqb (Algorithm 4) / svqbDrop (Algorithm 6) transform, device path.

@@ -38,6 +38,10 @@ int update_tc(cudaStream_t st, int64_t n, const SegList& S, const double* C, int
               void* work, int64_t work_bytes, const int* colexp = nullptr,
               int* status = nullptr);
 
+// One CTA whose bounded mbarrier wait (at most `limit` polls) on a phase that
+// nothing completes must run out: sets bit 0 of *status (device int).
+int wait_selftest(cudaStream_t st, int limit, int* status);
+
 // colexp[k] = E with max_i |S(i, k)| < 2^E over an n x s block (0 for zero columns).
 int column_exponents(cudaStream_t st, int64_t n, const SegList& Sg, int s, int* out);
 

@@ -170,10 +170,11 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count));
 }
 
-// Bounded wait for the completion of the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// Bounded wait for the completion of the mbarrier phase with the given parity
+// (at most `limit` polls); false when it ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int limit = kSpin) {
   uint32_t done = 0;
-  for (int spin = 0; spin < kSpin && !done; ++spin)
+  for (int spin = 0; spin < limit && !done; ++spin)
     asm volatile(
         "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
         "selp.b32 %0, 1, 0, P;\n\t}\n"
@@ -1087,7 +1088,26 @@ int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const
   return LOBPCG_OK;
 }
 
+// One CTA waits on the first phase of a barrier that expects one arrival and
+// gets none: the bounded wait must run out and report it in *status (bit 0),
+// as the Gram and update kernels do, and the CTA must return normally.
+__global__ void wait_selftest_kernel(int limit, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, limit)) atomicOr(status, 1);
+}
+
 }  // namespace
+
+int wait_selftest(cudaStream_t st, int limit, int* status) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit, status);
+  LOB_LAUNCHED();
+  return LOBPCG_OK;
+}
 
 int64_t gram_tc_workspace(int64_t n, int p, int q) {
   int slabs;

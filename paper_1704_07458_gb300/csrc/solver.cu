@@ -503,7 +503,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
   h->stats.orth_error = -1.0;
   const int64_t ld = h->ld;
   const int s = h->opt.omega_rows > 0 ? h->opt.omega_rows : 16;
-  const int maxit = h->opt.maxit > 0 ? h->opt.maxit : 2000;
+  const int maxit = h->opt.maxit > 0 ? h->opt.maxit : 6000;
   const double tau_ortho = h->opt.tau_ortho > 0 ? h->opt.tau_ortho : 100 * kEps;
   const double tau_skip = h->opt.tau_skip > 0 ? h->opt.tau_skip : 100 * kEps;
   const int refresh_every = h->opt.refresh_every > 0 ? h->opt.refresh_every : 50;
@@ -758,6 +758,8 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
           }
         }
       }
+      if (h->opt.inject_wait_timeout_at > 0 && it == h->opt.inject_wait_timeout_at)
+        LOB_CUDA_OK(cudaMemsetAsync(h->dstatus, 1, 1, h->st));  // bit 0, as a timed-out wait
       if (!(implicit && !refresh)) {
         if ((rc = apply_AB(h, h->Xn, (int)nx, h->AXn, h->b_kind ? h->BXn : nullptr))) return rc;
         if ((rc = apply_AB(h, h->Pn, npn, h->APn, h->b_kind ? h->BPn : nullptr))) return rc;

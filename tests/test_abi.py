@@ -77,6 +77,7 @@ def test_host_side_argument_errors_without_gpu(lib):
     assert lib.lobpcg_create(None, None, None) == gb.LOBPCG_ERR_ARG
     assert lib.lobpcg_get_stats(None, None) == gb.LOBPCG_ERR_ARG
     assert lib.lobpcg_last_error(None) == b"null handle"
+    assert lib.lobpcg_wait_selftest(0, None) == gb.LOBPCG_ERR_ARG
 
 
 class _FakeDeviceTensor:
