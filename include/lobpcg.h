@@ -237,7 +237,8 @@ int lobpcg_set_precond_callback(lobpcg_t h, lobpcg_precond_fn fn, void* ctx);
  *   X       n x k eigenvectors, row-major with leading dimension ldx, B-
  *           orthonormal, each sign-normalised so its largest-magnitude entry
  *           (lowest index on ties) is positive.
- *   iters   iterations of the main loop (host pointer, may be NULL).
+ *   iters   iterations of the main loop (host pointer, may be NULL); also written when the
+ *           solve ends with an error inside the loop (the iteration it stopped in).
  *   resnorm k backward errors of Eq. (9) from explicit products (mem_out; may be NULL).
  * Returns LOBPCG_ERR_NOT_CONVERGED (outputs valid) when maxit is reached. */
 int lobpcg_solve(lobpcg_t h, int64_t k, double tol, const double* X0, int64_t ldx0,

@@ -65,6 +65,23 @@ __device__ __forceinline__ double int_to_double(long long v, int e) {
   return __longlong_as_double((long long)bits);
 }
 
+// The same rounding for the common case of a normal result: one normalising
+// shift, and an integer add that carries a rounded-up mantissa into the
+// exponent field; zero, overflow and subnormal results take the path above.
+__device__ __forceinline__ double int_to_double_fast(long long v, int e) {
+  const unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+  if (a == 0) return 0.0;
+  const int lz = __clzll(a);
+  const int exp2 = e + 63 - lz;  // value in [2^exp2, 2^(exp2+1))
+  if (exp2 > 1022 || exp2 < -1022) return int_to_double(v, e);
+  const unsigned long long m = a << lz;  // leading one at bit 63
+  const unsigned long long mant = m >> 11;  // 53 bits, leading one at bit 52
+  const unsigned long long rest = m & 0x7FFULL;
+  const unsigned long long up = (rest > 0x400ULL || (rest == 0x400ULL && (mant & 1ULL))) ? 1ULL : 0ULL;
+  const unsigned long long bits = ((unsigned long long)(exp2 + 1022) << 52) + mant + up;
+  return __longlong_as_double((long long)(bits | (v < 0 ? 0x8000000000000000ULL : 0ULL)));
+}
+
 // (hi + lo) * 2^R + y0 (y0 may be 0), assembled in int64; error <= ~1 ulp.
 __device__ __forceinline__ double assemble_df(float hi, float lo, int R, double y0) {
   long long m[3];

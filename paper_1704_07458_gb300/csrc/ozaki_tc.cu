@@ -10,7 +10,8 @@
 // operations only.  No FP64 instruction runs on the hot path.
 //
 // GB300 mapping:
-//  * one CTA (256 threads, one CTA per SM) owns a 128 x NT output tile,
+//  * one CTA per SM owns a 128 x NT output tile (Gram: 256 threads; update:
+//    512 compute threads and one issuer warp),
 //    NT <= 96 a multiple of 16: tcgen05.mma kind::f16, M = 128, N = NT, K = 16;
 //  * the contraction runs in chunks of 16 (rows of U and V for the Gram,
 //    columns of S for the update), grouped in blocks of 256 that share one
@@ -22,9 +23,10 @@
 //    per block instead of once per chunk;
 //  * the raw FP64 operands stream into three shared-memory stages by cp.async,
 //    two chunks ahead of use, so that no thread waits on a global load; the
-//    digit planes have two stages: the tensor core multiplies chunk c while
-//    the 256 threads cut chunk c + 1; the digits of the small matrix C of the
-//    update are cut once per call and arrive by cp.async.bulk;
+//    tensor core multiplies chunk c while the compute threads cut chunk c + 1
+//    (two digit-plane stages in the Gram, three in the update); the digits of
+//    the small matrix C of the update are cut once per call and arrive by
+//    cp.async.bulk two chunks ahead;
 //  * the shared exponents come from a streaming pre-pass at full occupancy
 //    (per 256-row block and column for the Gram, per row for the update), so
 //    the tensor-core kernels never wait on a global load of their own;
@@ -83,18 +85,14 @@ template <int S>
 __device__ __forceinline__ void digits(double x, int E, float (&d)[S]) {
   const long long bits = __double_as_longlong(x);
   const int be = (int)((bits >> 52) & 0x7FF);
-  long long mant = bits & 0x000FFFFFFFFFFFFFLL;
-  if (be != 0) mant |= 0x0010000000000000LL;
-  const int sh = max(be, 1) - 1076 + 8 * S - E;
-  long long F;
-  if (sh >= 0) {
-    F = mant << min(sh, 10);  // sh <= 2 whenever |x| < 2^E
-  } else {
-    const int r = -sh;
-    F = r > 62 ? 0 : ((mant >> (r - 1)) + 1) >> 1;
-  }
-  if (bits < 0) F = -F;
-  const long long G = F + digit_bias<S>();
+  const long long mant = (bits & 0x000FFFFFFFFFFFFFLL) | ((long long)(be != 0) << 52);
+  // F = round(mant 2^sh), sh = max(be, 1) - 1076 + 8S - E <= 2 whenever
+  // |x| < 2^E (a zero x gives F = 0 for any sh).  Branch-free: with
+  // v = mant 2^3 < 2^56 and t = 2 - sh clamped to [0, 63],
+  // F = ((v >> t) + 1) >> 1 (round half up in magnitude).
+  const int t = min(max(2 - (max(be, 1) - 1076 + 8 * S - E), 0), 63);
+  const long long F = (((mant << 3) >> t) + 1) >> 1;
+  const long long G = digit_bias<S>() + (bits < 0 ? -F : F);
   const uint32_t lo = (uint32_t)G, hi = (uint32_t)((unsigned long long)G >> 32);
 #pragma unroll
   for (int s = 1; s < S; ++s) {
@@ -253,7 +251,7 @@ __device__ __forceinline__ long long shr_sat(long long v, int k) {
 
 // v * 2^e + y0 rounded to FP64 (error below 1 ulp), integer operations only.
 __device__ __forceinline__ double assemble_i64(long long v, int e, double y0) {
-  if (y0 == 0.0) return int_to_double(v, e);
+  if ((__double_as_longlong(y0) << 1) == 0) return int_to_double_fast(v, e);  // y0 = +-0, no FP64 op
   long long my;
   int ey;
   double_parts(y0, my, ey);
@@ -687,9 +685,14 @@ __global__ void split_c_tc_kernel(const double* __restrict__ C, int64_t ldc, int
 }
 
 constexpr int kRawRow = TCK + 1;  // raw row pitch in doubles (odd: conflict-free 8-byte reads)
+constexpr int kUThr = 512;        // compute threads of the update (16 warps)
+constexpr int kUThrAll = kUThr + 32;  // + one issuer warp
+constexpr int kUIssuer = kUThr;   // issuer thread of the update (warp 16, lane 0)
+constexpr int kUStages = 3;       // digit-plane stages of A and B (chunks in flight)
+constexpr int kUCols = NTMAX / 32 * 8;  // output columns of one thread (8-column groups cg + 4 i)
 
 struct UpdShared {
-  unsigned long long bfull[2], mdone[2];
+  unsigned long long bfull[kUStages], mdone[kUStages];
   uint32_t tmem_base;
   int fail;
   int eA[TCM];     // row exponent bounds of the balanced S, current tile
@@ -698,40 +701,33 @@ struct UpdShared {
 };
 
 // ER[i] = exponent bound of row i of the balanced S(i, k) 2^-colexp[k] over all
-// k (kEZero for a zero row).  One warp per row, lanes over k.
+// k (kEZero for a zero row).  One warp per row, lanes over the columns of each
+// segment in turn (plain pointer arithmetic within a segment).
 __global__ void row_exp_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
                                int* __restrict__ ER) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
   int e = -1000000;
-  for (int k0 = 0; k0 < s; k0 += 128) {
-    double x[4];
-    int cxk[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = k0 + 32 * i + lane;
-      x[i] = 0.0;
-      cxk[i] = 0;
-      if (k < s) {
-        const double* p;
-        long long ld;
-        seg_col_ptr(Sg, k, &p, &ld);
-        x[i] = __ldg(p + row * ld);
-        cxk[i] = colexp ? __ldg(colexp + k) : 0;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const long long b = __double_as_longlong(x[i]);
-      if ((b << 1) != 0) e = max(e, max((int)((b >> 52) & 0x7FF), 1) - cxk[i]);
+  for (int g = 0; g < kMaxSeg; ++g) {
+    if (g >= Sg.nseg) break;
+    const int c0 = Sg.off[g], w = Sg.off[g + 1] - c0;
+    const double* base = Sg.ptr[g] + row * Sg.ld[g];
+    for (int c = lane; c < w; c += 64) {  // two loads in flight per lane
+      const bool two = c + 32 < w;
+      const long long b0 = __double_as_longlong(__ldg(base + c));
+      const long long b1 = two ? __double_as_longlong(__ldg(base + c + 32)) : 0LL;
+      const int x0 = colexp ? __ldg(colexp + c0 + c) : 0;
+      const int x1 = (colexp && two) ? __ldg(colexp + c0 + c + 32) : 0;
+      if ((b0 << 1) != 0) e = max(e, max((int)((b0 >> 52) & 0x7FF), 1) - x0);
+      if ((b1 << 1) != 0) e = max(e, max((int)((b1 >> 52) & 0x7FF), 1) - x1);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (lane == 0) ER[row] = e > -1000000 ? e - 1022 : kEZero;
 }
-
 
 __device__ __forceinline__ void upd_k(const UpdShared& sh, int k, const double** p,
                                       long long* ld) {
@@ -742,71 +738,98 @@ __device__ __forceinline__ void upd_k(const UpdShared& sh, int k, const double**
 // ([TCM][kRawRow]); zero outside the matrix.
 __device__ __forceinline__ void upd_stage_raw(const UpdShared& sh, int64_t n, int s, int64_t row0,
                                               int kc, uint32_t raw, int tid) {
-  // thread: column kk = tid % TCK, rows tid / TCK + 16 j (coalesced along k)
+  // thread: column kk = tid % TCK, rows tid / TCK + 32 j (coalesced along k)
   const int kk = tid % TCK, r0 = tid / TCK;
   const int k = kc + kk;
   const double* p;
   long long ld;
   upd_k(sh, k < s ? k : 0, &p, &ld);
   const double* src = p + (row0 + r0) * ld;
-  const long long step = (long long)(kThr / TCK) * ld;
+  const long long step = (long long)(kUThr / TCK) * ld;
 #pragma unroll
-  for (int j = 0; j < TCM * TCK / kThr; ++j) {
-    const int rl = r0 + j * (kThr / TCK);
+  for (int j = 0; j < TCM * TCK / kUThr; ++j) {
+    const int rl = r0 + j * (kUThr / TCK);
     const bool ok = k < s && row0 + rl < n;
     cp_async8(raw + (uint32_t)(rl * kRawRow + kk) * 8, ok ? src : p, ok);
     src += step;
   }
 }
 
-constexpr int kThrAll = kThr + 32;  // 8 compute warps + 1 issuer warp
-constexpr int kIssuerW = kThr;      // issuer thread of the update (warp 8, lane 0)
-constexpr int kOutRows = 128;       // rows of the output staging pass (the whole tile)
+// 4 consecutive K values of one M index -> S planes, one 8-byte shared store
+// per plane (half a K-major core-matrix row).
+template <int S>
+__device__ __forceinline__ void split4(const double (&x)[4], const int (&E)[4], uint32_t dst,
+                                       uint32_t pstride) {
+  uint32_t w[S][2];
+#pragma unroll
+  for (int i = 0; i < 4; i += 2) {
+    float a[S], b[S];
+    digits<S>(x[i], E[i], a);
+    digits<S>(x[i + 1], E[i + 1], b);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl)
+      w[sl][i >> 1] = __byte_perm(__float_as_uint(a[sl]), __float_as_uint(b[sl]), 0x7632);
+  }
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl)
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};\n" ::"r"(dst + sl * pstride), "r"(w[sl][0]),
+                 "r"(w[sl][1])
+                 : "memory");
+}
 
 template <int S>
 __host__ __device__ inline size_t upd_regionA(int NT) {
-  const size_t a = 2 * S * planeA_bytes<S>(), o = (size_t)kOutRows * (NT + 1) * 8;
-  return ((a > o ? a : o) + 1023) / 1024 * 1024;
+  const size_t a = (size_t)kUStages * S * planeA_bytes<S>();
+  return (a + 1023) / 1024 * 1024;
 }
 
 template <int S>
 size_t upd_smem_bytes(int NT, int s) {
-  return upd_regionA<S>(NT) + 2 * S * planeB_bytes(NT) + (size_t)kRaw * TCM * kRawRow * 8 +
-         sizeof(UpdShared) + (size_t)round_up(std::max(s, 1), 4) * 4 + 1024;
+  return upd_regionA<S>(NT) + (size_t)kUStages * S * planeB_bytes(NT) +
+         (size_t)kRaw * TCM * kRawRow * 8 + sizeof(UpdShared) +
+         (size_t)round_up(std::max(s, 1), 4) * 4 + 1024;
 }
 
+// One CTA per SM: 16 compute warps cut the staged S chunks into digit planes
+// and convert the TMEM accumulators; one issuer thread (warp 16) issues the
+// MMAs and the bulk copies of C's digits.  Three plane stages: the issuer
+// fetches C's digits of chunk g + 2 while the tensor core multiplies chunk g
+// and the compute warps cut chunk g + 1.
 // kOneBlock: s <= 256, a single exponent block; the TMEM accumulators go
 // straight to the output (no int64 carry registers).
+// 17 warps: the busiest of the four SM sub-partitions holds five, so the
+// register cap is 16,384 / (5 x 32) -> 96 per thread (the multi-block
+// variant spills its int64 carries a little; the s <= 256 one does not)
 template <int S, bool kOneBlock>
-__global__ void __launch_bounds__(kThrAll, 1)
+__global__ void __launch_bounds__(kUThrAll, 1)
     ozaki_update_tc_kernel(int64_t n, SegList Sg, int s, const int* __restrict__ colexp,
                            const uint16_t* __restrict__ Cs, const int* __restrict__ Ce,
                            const int* __restrict__ ER, int m, int ntiles, int NT,
                            int64_t ntile_total, double beta, SegList Y0, OutList Y,
                            int* status) {
   constexpr int NA = nacc<S>();
+  constexpr int NS = kUStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const uint32_t pa = (uint32_t)planeA_bytes<S>(), pb = (uint32_t)planeB_bytes(NT);
   const size_t regA = upd_regionA<S>(NT);
-  // region A: the A planes of both stages, reused as the output staging area
+  // region A: the A planes of the stages
   const uint32_t aS0 = smem_u32(base), bS0 = smem_u32(base) + (uint32_t)regA;
-  double* ostage = reinterpret_cast<double*>(base);
-  const int OP = NT + 1;  // output staging pitch (odd: conflict-free row-wise writes)
-  const uint32_t raw0 = bS0 + 2 * S * pb;
+  const uint32_t raw0 = bS0 + NS * S * pb;
   constexpr uint32_t rawB = TCM * kRawRow * 8;
-  unsigned char* after_raw = base + regA + 2 * S * pb + kRaw * rawB;
+  unsigned char* after_raw = base + regA + (size_t)NS * S * pb + kRaw * rawB;
   UpdShared& sh = *reinterpret_cast<UpdShared*>(after_raw);
   int* cx = reinterpret_cast<int*>(after_raw + sizeof(UpdShared));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool compute = tid < kThr;
+  const bool compute = tid < kUThr;
+  const bool has_y0 = beta != 0.0;  // the kernel's only FP64 operation
   const int nch = (int)ceil_div(s, TCK);
   const size_t cs_blk = (size_t)S * KG * (NT / 8) * 64;  // bf16 per (chunk, tile)
   const uint32_t bbytes = (uint32_t)(cs_blk * 2);
 
   if (warp == 0) tmem_alloc(smem_u32(&sh.tmem_base));
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(smem_u32(&sh.bfull[i]), 1);
       mbar_init(smem_u32(&sh.mdone[i]), 1);
     }
@@ -814,34 +837,56 @@ __global__ void __launch_bounds__(kThrAll, 1)
     sh.seg = Sg;
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
-  for (int k = tid; k < s; k += kThrAll) cx[k] = colexp ? colexp[k] : 0;
+  for (int k = tid; k < s; k += kUThrAll) cx[k] = colexp ? colexp[k] : 0;
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = sh.tmem_base;
 
-  const int my_r = 32 * (warp & 3) + lane;  // TMEM lane = tile row (compute threads)
-  const int half = NT / 2;
-  const int j0 = half * ((warp >> 2) & 1);
-  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  // digit split: row rl of the tile, columns 4 kq .. 4 kq + 3 of the chunk
+  // (lane pairs share a row: a warp's 8-byte plane stores are contiguous)
+  const int rl = 16 * (warp & 7) + (lane >> 1), kq = 2 * ((warp >> 3) & 1) + (lane & 1);
+  const uint32_t aoff =
+      (uint32_t)(((kq >> 1) * (TCM / 8) + (rl >> 3)) * 128 + (rl & 7) * 16 + (kq & 1) * 8);
+  // epilogue: TMEM lane quarter q (tile rows 32 q ..), 8-column groups cg + 4 i
+  const int q = warp & 3, cg = (warp >> 2) & 3;
+  const int my_r = 32 * q + lane;
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
   bool failed = false;
   int64_t gc = 0;  // chunk counter of this CTA over all its tiles
   const int64_t t0 = blockIdx.x, tstep = gridDim.x;
   auto tile_row0 = [&](int64_t t) { return (t / ntiles) * TCM; };
   const int64_t my_chunks = ((ntile_total - t0 + tstep - 1) / tstep) * nch;
-  // chunk g of this CTA: tile t0 + (g / nch) tstep, columns (g % nch) TCK
-  auto stage = [&](int64_t g) {
-    if (g < my_chunks) {
-      const int64_t t = t0 + (g / nch) * tstep;
-      upd_stage_raw(sh, n, s, tile_row0(t), (int)(g % nch) * TCK,
-                    raw0 + (uint32_t)(g % kRaw) * rawB, tid);
-    }
+  // chunk g of this CTA: tile t0 + (g / nch) tstep, columns (g % nch) TCK;
+  // plane stage g % NS, used for the (g / NS)-th time.  Staging (every
+  // compute thread) and the B copies (issuer) each walk the chunks in order,
+  // so their positions advance by one chunk per call: no division by a
+  // runtime value per chunk (64-bit division is a long software sequence).
+  int64_t st_g = 0, st_t = t0, st_row0 = tile_row0(t0);
+  int st_c = 0, st_slot = 0;
+  auto stage_next = [&]() {  // raw S of chunk st_g into raw stage st_g % kRaw
+    if (st_g < my_chunks)
+      upd_stage_raw(sh, n, s, st_row0, st_c * TCK, raw0 + (uint32_t)st_slot * rawB, tid);
     cp_async_commit();
+    ++st_g;
+    st_slot = st_slot + 1 == kRaw ? 0 : st_slot + 1;
+    if (++st_c == nch) {
+      st_c = 0;
+      st_t += tstep;
+      st_row0 = tile_row0(st_t);
+    }
   };
-  auto load_b = [&](int64_t g) {  // issuer: B digits of chunk g into stage g & 1
-    const int64_t t = t0 + (g / nch) * tstep;
-    const uint32_t st = (uint32_t)(g & 1);
-    const size_t src = ((size_t)(g % nch) * ntiles + (size_t)(t % ntiles)) * cs_blk;
+  int64_t lb_g = 0, lb_t = t0;
+  int lb_c = 0, lb_tile = (int)(t0 % ntiles);
+  auto load_b_next = [&]() {  // issuer: B digits of chunk lb_g into stage lb_g % NS
+    const uint32_t st = (uint32_t)(lb_g % NS);
+    const size_t src = ((size_t)lb_c * ntiles + (size_t)lb_tile) * cs_blk;
+    ++lb_g;
+    if (++lb_c == nch) {
+      lb_c = 0;
+      lb_t += tstep;
+      lb_tile = (int)(lb_t % ntiles);
+    }
     uint64_t state;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
                  : "=l"(state)
@@ -853,14 +898,18 @@ __global__ void __launch_bounds__(kThrAll, 1)
         "l"(Cs + src), "r"(bbytes), "r"(smem_u32(&sh.bfull[st]))
         : "memory");
   };
+  auto parity = [](int64_t g) { return (uint32_t)((g / NS) & 1); };
   int64_t b_issued = -1;  // last chunk whose B copy the issuer started
+  int64_t m_issued = -1;  // last chunk whose MMAs the issuer committed
   if (compute) {
-    stage(0);
-    stage(1);
+    stage_next();
+    stage_next();
     cp_async_wait1();
-  } else if (tid == kIssuerW && my_chunks > 0) {
-    load_b(0);
-    b_issued = 0;
+  } else if (tid == kUIssuer) {
+    for (int64_t g = 0; g < 2 && g < my_chunks; ++g) {
+      load_b_next();
+      b_issued = g;
+    }
   }
   __syncthreads();
 
@@ -869,42 +918,37 @@ __global__ void __launch_bounds__(kThrAll, 1)
     const int64_t row0 = tile_row0(t);
     const int tn = tile * NT;
     const int nq_ = min(NT, m - tn);
-    for (int r = tid; r < TCM; r += kThrAll) sh.eA[r] = row0 + r < n ? ER[row0 + r] : kEZero;
-    for (int j = tid; j < NTMAX; j += kThrAll) sh.eC[j] = j < NT ? Ce[tn + j] : kEZero;
+    for (int r = tid; r < TCM; r += kUThrAll) sh.eA[r] = row0 + r < n ? ER[row0 + r] : kEZero;
+    for (int j = tid; j < NTMAX; j += kUThrAll) sh.eC[j] = j < NT ? Ce[tn + j] : kEZero;
     __syncthreads();
-    long long acc[kOneBlock ? 1 : NTMAX / 2];
+    long long acc[kOneBlock ? 1 : kUCols];
 #pragma unroll
-    for (int j = 0; j < (kOneBlock ? 1 : NTMAX / 2); ++j) acc[j] = 0;
+    for (int j = 0; j < (kOneBlock ? 1 : kUCols); ++j) acc[j] = 0;
     uint32_t started = 0;
     for (int kc = 0; kc < s && !failed; kc += kBlock) {  // blocks of 256 columns
       started = 0;
       const int kend = min(s, kc + kBlock);
       const bool last_block = kend >= s;
       for (int k1 = kc; k1 < kend; k1 += TCK) {
-        const uint32_t st = (uint32_t)(gc & 1);
+        const uint32_t st = (uint32_t)(gc % NS);
         if (compute) {
           const uint32_t raw = raw0 + (uint32_t)(gc % kRaw) * rawB;
-          if (gc >= 2 && !mbar_wait(smem_u32(&sh.mdone[st]), (uint32_t)((gc >> 1) - 1) & 1))
-            sh.fail = 1;
-          // cut the staged chunk: item (row, 8-column group) = (tid % 128, tid / 128)
+          // the stage's planes are free once the MMAs of chunk gc - NS are done
+          if (gc >= NS && !mbar_wait(smem_u32(&sh.mdone[st]), parity(gc - NS))) sh.fail = 1;
           {
-            const int rl = tid % TCM, kg = tid / TCM;
-            double x[8];
-            int E[8];
+            double x[4];
+            int E[4];
             const int Er = sh.eA[rl];
-            const uint32_t src = raw + (uint32_t)(rl * kRawRow + kg * 8) * 8;
+            const uint32_t src = raw + (uint32_t)(rl * kRawRow + kq * 4) * 8;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < 4; ++i) {
               ld_shared_f64(src + 8 * i, x[i]);
-              const int k = k1 + kg * 8 + i;
+              const int k = k1 + kq * 4 + i;
               E[i] = Er + (k < s ? cx[k] : 0);
             }
-            split8<S>(x, E,
-                      aS0 + st * S * pa +
-                          (uint32_t)((kg * (TCM / 8) + (rl >> 3)) * 128 + (rl & 7) * 16),
-                      pa);
+            split4<S>(x, E, aS0 + st * S * pa + aoff, pa);
           }
-          stage(gc + 2);
+          stage_next();  // chunk gc + 2
           cp_async_wait1();
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         }
@@ -912,21 +956,22 @@ __global__ void __launch_bounds__(kThrAll, 1)
           failed = true;
           break;
         }
-        if (tid == kIssuerW) {
-          if (!mbar_wait(smem_u32(&sh.bfull[st]), (uint32_t)(gc >> 1) & 1)) {
+        if (tid == kUIssuer) {
+          if (!mbar_wait(smem_u32(&sh.bfull[st]), parity(gc))) {
             sh.fail = 1;
           } else {
             asm volatile("tcgen05.fence::after_thread_sync;\n");
             issue_chunk<S>(tmem, NT, aS0 + st * S * pa, bS0 + st * S * pb, started);
             mma_commit(smem_u32(&sh.mdone[st]));
-            // B of the next chunk into the other stage, once chunk gc - 1 is done
-            if (gc + 1 < my_chunks) {
+            m_issued = gc;
+            // B of chunk gc + 2 into the stage of chunk gc - 1 once its MMAs are done
+            if (gc + 2 < my_chunks) {
               if (gc >= 1 &&
-                  !mbar_wait(smem_u32(&sh.mdone[st ^ 1]), (uint32_t)((gc - 1) >> 1) & 1)) {
+                  !mbar_wait(smem_u32(&sh.mdone[(gc - 1) % NS]), parity(gc - 1))) {
                 sh.fail = 1;
               } else {
-                load_b(gc + 1);
-                b_issued = gc + 1;
+                load_b_next();  // chunk gc + 2
+                b_issued = gc + 2;
               }
             }
           }
@@ -934,8 +979,7 @@ __global__ void __launch_bounds__(kThrAll, 1)
         ++gc;
       }
       if (failed) break;
-      if (!mbar_wait(smem_u32(&sh.mdone[(gc - 1) & 1]), (uint32_t)((gc - 1) >> 1) & 1))
-        sh.fail = 1;
+      if (!mbar_wait(smem_u32(&sh.mdone[(gc - 1) % NS]), parity(gc - 1))) sh.fail = 1;
       if (__syncthreads_or(sh.fail)) {
         failed = true;
         break;
@@ -944,18 +988,19 @@ __global__ void __launch_bounds__(kThrAll, 1)
       if (!last_block) {
         if (!kOneBlock && compute) {
 #pragma unroll
-          for (int g = 0; g < NTMAX / 16; ++g) {
-            if (8 * g < half) {
+          for (int i = 0; i < kUCols / 8; ++i) {
+            const int g = cg + 4 * i;
+            if (8 * g < NT) {
               float v[NA][8];
 #pragma unroll
-              for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + j0 + 8 * g, v[a]);
+              for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + 8 * g, v[a]);
               asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
+              for (int c = 0; c < 8; ++c) {
                 float w[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int a = 0; a < NA; ++a) w[a] = v[a][i];
-                if (!kOneBlock) acc[(8 * g + i) % (kOneBlock ? 1 : NTMAX / 2)] += acc_to_i64<S>(w);
+                for (int a = 0; a < NA; ++a) w[a] = v[a][c];
+                if (!kOneBlock) acc[(8 * i + c) % (kOneBlock ? 1 : kUCols)] += acc_to_i64<S>(w);
               }
             }
           }
@@ -964,68 +1009,61 @@ __global__ void __launch_bounds__(kThrAll, 1)
         __syncthreads();
       }
     }
-    // ---- output: Y = acc 2^(E_row + E_col - 14 - kFrac) + beta Y0, staged
-    // through shared memory (coalesced Y0 and Y) in passes of kOutRows rows;
-    // in a pass every compute warp whose TMEM lane quarter lies in it converts
-    // (with kOutRows = TCM all eight warps convert at once)
-    for (int h = 0; h < TCM / kOutRows; ++h) {
-      const int64_t rbase = row0 + h * kOutRows;
-      if (beta != 0.0 && compute && !failed) {
-        for (int rr = warp; rr < kOutRows; rr += kThr / 32) {
-          const int64_t row = rbase + rr;
-          if (row < n)
-            for (int j = lane; j < nq_; j += 32) ostage[rr * OP + j] = seg_load(Y0, tn + j, row);
-        }
-      }
-      __syncthreads();
-      if (compute && (32 * (warp & 3)) / kOutRows == h) {
-        const int rr = my_r - h * kOutRows;
-        const int Er = sh.eA[my_r];
+    // ---- output: Y = acc 2^(E_row + E_col - 14 - kFrac) + beta Y0.  All
+    // sixteen compute warps convert at once: a warp owns its TMEM lane
+    // quarter's 32 rows and the 8-column groups cg + 4 i, and each thread
+    // stores the 8 consecutive outputs of its row per group straight to
+    // global memory (no staging pass, no barrier between conversion and
+    // store)
+    if (compute) {
+      const int64_t row = row0 + my_r;
+      const bool live = row < n;
+      const int Er = sh.eA[my_r];
 #pragma unroll
-        for (int g = 0; g < NTMAX / 16; ++g) {
-          if (8 * g < half) {
-            float v[NA][8];
-            if (!failed) {
+      for (int i = 0; i < kUCols / 8; ++i) {
+        const int g = cg + 4 * i;
+        if (8 * g < NT) {  // warp-uniform: the TMEM loads are .sync.aligned
+          float v[NA][8];
+          if (!failed) {
 #pragma unroll
-              for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + j0 + 8 * g, v[a]);
-              asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            }
+            for (int a = 0; a < NA; ++a) tmem_ld8(tmem + lane_off + a * NT + 8 * g, v[a]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          }
+          if (live) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int j = j0 + 8 * g + i;
+            for (int c = 0; c < 8; ++c) {
+              const int j = 8 * g + c;
               if (j < nq_) {
                 double out = __longlong_as_double(0x7FF8000000000000LL);
                 if (!failed) {
                   float w[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                  for (int a = 0; a < NA; ++a) w[a] = v[a][i];
+                  for (int a = 0; a < NA; ++a) w[a] = v[a][c];
                   long long T = acc_to_i64<S>(w);
-                  if (!kOneBlock) T += acc[(8 * g + i) % (kOneBlock ? 1 : NTMAX / 2)];
-                  const double y0 = beta != 0.0 ? ostage[rr * OP + j] : 0.0;
+                  if (!kOneBlock) T += acc[(8 * i + c) % (kOneBlock ? 1 : kUCols)];
+                  const double y0 = has_y0 ? seg_load(Y0, tn + j, row) : 0.0;
                   out = assemble_i64(T, Er + sh.eC[j] - 14 - kFrac, y0);
                 }
-                ostage[rr * OP + j] = out;
+                *out_addr(Y, tn + j, row) = out;
               }
             }
           }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;\n");
-      __syncthreads();
-      if (compute) {
-        for (int rr = warp; rr < kOutRows; rr += kThr / 32) {
-          const int64_t row = rbase + rr;
-          if (row < n)
-            for (int j = lane; j < nq_; j += 32) *out_addr(Y, tn + j, row) = ostage[rr * OP + j];
-        }
-      }
-      __syncthreads();
     }
+    // TMEM and the tile's exponents are reused by the next tile
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
   }
   if (compute) cp_async_wait0();  // no copy may outlive the CTA
   if (tid == 0 && failed && status) atomicOr(status, 1);
-  if (tid == kIssuerW && b_issued >= 0 && failed)
-    mbar_wait(smem_u32(&sh.bfull[b_issued & 1]), (uint32_t)(b_issued >> 1) & 1);
+  if (tid == kUIssuer && failed) {
+    // drain what is still in flight: the B copies not yet consumed and the
+    // last committed MMAs (bounded waits; their outcome no longer matters)
+    for (int64_t g = m_issued + 1; g <= b_issued; ++g)
+      mbar_wait(smem_u32(&sh.bfull[g % NS]), parity(g));
+    if (m_issued >= 0) mbar_wait(smem_u32(&sh.mdone[m_issued % NS]), parity(m_issued));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0) {
@@ -1079,10 +1117,10 @@ int update_tc_launch(cudaStream_t st, int64_t n, const SegList& Sg, int s, const
   const int64_t tiles = ceil_div(n, TCM) * ntiles;
   const int64_t grid = std::min<int64_t>(tiles, 152);
   if (s <= kBlock)
-    ozaki_update_tc_kernel<S, true><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
+    ozaki_update_tc_kernel<S, true><<<(unsigned)grid, kUThrAll, upd_smem_bytes<S>(NT, s), st>>>(
         n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y, status);
   else
-    ozaki_update_tc_kernel<S, false><<<(unsigned)grid, kThrAll, upd_smem_bytes<S>(NT, s), st>>>(
+    ozaki_update_tc_kernel<S, false><<<(unsigned)grid, kUThrAll, upd_smem_bytes<S>(NT, s), st>>>(
         n, Sg, s, colexp, Cs, Ce, ER, m, ntiles, NT, tiles, beta, Y0, Y, status);
   LOB_LAUNCHED();
   return LOBPCG_OK;

@@ -637,6 +637,7 @@ int solve_impl(lobpcg_ctx* h, int64_t k, double tol, const double* X0, int64_t l
         break;
       }
       ++it;
+      h->stats.iterations = it;  // also what an error return reports
       int nw = (int)(nx - nc);
       // which blocks of the projected pencil are computed rather than taken
       // from the identities (12)-(14): the W columns (Algorithm 8), P and W
@@ -1286,7 +1287,9 @@ LOBPCG_EXPORT int lobpcg_solve(lobpcg_t h, int64_t k, double tol, const double* 
   cudaGetDevice(&dev);
   if (dev != h->device) return h->fail(LOBPCG_ERR_ARG, "handle belongs to another device");
   h->err.clear();
+  h->stats.iterations = 0;
   int rc = solve_impl(h, k, tol, X0, ldx0, seed, mem_in, lambda, X, ldx, mem_out, iters, resnorm);
+  if (rc && rc != LOBPCG_ERR_NOT_CONVERGED && iters) *iters = h->stats.iterations;
   if (rc == LOBPCG_ERR_CUDA && h->err.empty()) {
     cudaError_t e = cudaGetLastError();
     h->err = std::string("CUDA error: ") + cudaGetErrorString(e);

@@ -54,6 +54,21 @@ def _solve(p, **opts):
     return (lam.cpu().numpy(), X.cpu().numpy(), int(it), be.cpu().numpy(), rc, st)
 
 
+def _solve_dev(p, **opts):
+    """As _solve, outputs left on the device (torch tensors)."""
+    torch = torch_cuda()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s = gb.Solver(**opts)
+    s.set_operator(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val),
+                   b_diag=None if p.b_diag is None else dev(p.b_diag))
+    nx = synth.block_width(p.k, p.n)
+    X0 = dev(synth.normal_block(0, synth.STREAM_X0, p.n, nx))
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, device=True, raise_on_error=False)
+    st = s.stats()
+    s.close()
+    return lam, X, int(it), be, rc, st
+
+
 def _check_eq9(p, lam, X, normA, normB):
     A = sp.csr_matrix((p.A.val, p.A.col, p.A.rowptr), shape=(p.n, p.n))
     BX = X if p.b_diag is None else p.b_diag[:, None] * X
@@ -105,10 +120,57 @@ def test_c5_full_size_default_form_matches_stored_oracle():
     the identities (12)-(14) assume)."""
     p = synth.make_problem("lap2d_512_V")
     ref, meta = _golden("lap2d_512_V")
-    lam, X, it, be, rc, st = _solve(p)
+    lam, X, it, be, rc, st = _solve(p, gemm_mode="ozaki_tc")
     assert rc == gb.LOBPCG_OK, rc
     assert st["explicit_rr_calls"] > 0
     rel = np.abs(lam - ref) / np.abs(ref)
     assert rel.max() <= 1e-9, (rel.max(), int(np.argmax(rel)))
     orth = _check_eq9(p, lam, X, meta["norm_a"], meta["norm_b"])
     assert orth <= 1e-10, orth
+
+
+def _properties_on_device(p, lam, X, st, tol_orth):
+    """Explicit FP64 Eq. (9) and X^T X = I for B = I, computed on the device
+    with torch's own sparse and dense products (independent of the library)."""
+    torch = torch_cuda()
+    A = torch.sparse_csr_tensor(torch.from_numpy(p.A.rowptr.astype(np.int64)),
+                                torch.from_numpy(p.A.col.astype(np.int64)),
+                                torch.from_numpy(p.A.val), size=(p.n, p.n)).cuda()
+    R = (A @ X) - X * lam[None, :]
+    be = torch.linalg.norm(R, dim=0) / (
+        (st["norm_a"] + lam.abs() * st["norm_b"]) * torch.linalg.norm(X, dim=0))
+    del R
+    assert float(be.max()) <= p.tol * (1 + 1e-6), float(be.max())
+    G = X.T @ X
+    G -= torch.eye(p.k, dtype=G.dtype, device=G.device)
+    orth = float(G.abs().max())
+    assert orth <= tol_orth, orth
+    assert bool(torch.all(lam[1:] >= lam[:-1] - 1e-14))
+    return float(be.max()), orth
+
+
+def test_c3_full_size_properties():
+    """128^3 log-normal diffusion (sigma = 1), B = I, Jacobi K, k = 256,
+    tol 1e-8, default form: explicit Eq. (9), X^T X = I, and the spectrum of
+    the SPD operator positive.  No closed form: the oracle's eigenvalues are
+    compared at 16^3 in test_gpu_solve."""
+    p = synth.make_problem("diffusion_128")
+    lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
+    assert rc == gb.LOBPCG_OK, rc
+    bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
+    assert float(lam[0]) > 0
+    print(f"c3: {it} iterations, max backward error {bmax:.3e}, |X^T X - I| {orth:.2e}")
+
+
+def test_c4_full_size_properties():
+    """-1/2 Laplacian (periodic 96^3) + V, V ~ U[0, 10], k = 1024 (n_x = 1127,
+    projected pencils of order up to 3381), tol 1e-8, default form: explicit
+    Eq. (9), X^T X = I, and 0 <= lambda <= 16 (the spectrum of -1/2 Laplacian
+    lies in [0, 6], V in [0, 10])."""
+    p = synth.make_problem("hamiltonian_96")
+    lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
+    assert rc == gb.LOBPCG_OK, rc
+    bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
+    assert float(lam[0]) >= 0 and float(lam[-1]) <= 16
+    print(f"c4: {it} iterations, max backward error {bmax:.3e}, |X^T X - I| {orth:.2e}, "
+          f"dropped columns {st['dropped_columns']}, switch at {st['flip_iteration']}")

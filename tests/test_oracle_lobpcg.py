@@ -485,3 +485,33 @@ def test_lobpcg_with_chebyshev_precond_converges_faster():
     np.testing.assert_allclose(r.lam, p.closed_form[:p.k], rtol=1e-10)
     _, rj = _run(p)
     assert r.iters < rj.iters
+
+
+def test_zero_b_norm_column_reading():
+    """A column of zero B-norm gets D_jj = 0 (Algorithm 4 leaves D undefined
+    there): svqb (Algorithm 4) returns it as a zero column beside B-orthonormal
+    ones, svqbDrop (Algorithm 6) drops it through its own threshold, and
+    orthoDrop (Algorithm 5) returns a B-orthonormal block without it."""
+    rng = np.random.default_rng(7)
+    n = 200
+    b = _rand_metric(n, rng)
+    Bm = lambda Y: b[:, None] * Y
+    U = rng.standard_normal((n, 5))
+    U[:, 2] = 0.0
+    T = L.svqb(U, Bm(U), n * L.EPS)
+    # the zero column comes out as rounding (eigenvector mixing of ~eps,
+    # divided by the replaced sqrt(theta)): zero up to 1e-8
+    norms = np.sqrt(np.einsum("ij,ij->j", T, Bm(T)))
+    assert np.sum(norms < 1e-8) == 1 and np.all(np.isfinite(T))
+    Tk = T[:, norms >= 1e-8]
+    np.testing.assert_allclose(Tk.T @ Bm(Tk), np.eye(4), atol=1e-12)
+    Td = L.svqb_drop(U, Bm(U), n * L.EPS)
+    assert Td.shape[1] == 4
+    np.testing.assert_allclose(Td.T @ Bm(Td), np.eye(4), atol=1e-12)
+    V0 = rng.standard_normal((n, 3))
+    C, _ = L.rayleigh_ritz(V0.T @ V0, V0.T @ Bm(V0))
+    V = V0 @ C
+    W, BW = L.ortho_drop(Bm, U, V, Bm(V), 100 * L.EPS)
+    assert W.shape[1] == 4
+    np.testing.assert_allclose(W.T @ Bm(W), np.eye(4), atol=1e-12)
+    np.testing.assert_allclose(V.T @ Bm(W), 0, atol=1e-12)
