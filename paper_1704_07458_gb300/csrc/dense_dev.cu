@@ -373,31 +373,38 @@ __global__ void __launch_bounds__(1024, 1) tridiag32_full_kernel(int n, const do
     __syncthreads();
     const float tk = s_tau;
     if (tk == 0.f) continue;
-    // p_i = tau sum_j A22(i, j) v_j, one thread per row
+    // p_i = tau sum_j A22(i, j) v_j: four consecutive lanes per row, lane
+    // sub of a row takes the j = sub (mod 4) terms of the stored lower
+    // triangle (row part j <= i, column part j > i), a shuffle sums them
     float pv = 0.f;
-    if (t < m) {
-      const int gi = o + t;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const float* row = F + gi * ld + o;  // A(gi, o + j), j <= t
-      int j = 0;
-      for (; j + 3 <= t; j += 4) {
-        a0 = fmaf(row[j], v[j], a0);
-        a1 = fmaf(row[j + 1], v[j + 1], a1);
-        a2 = fmaf(row[j + 2], v[j + 2], a2);
-        a3 = fmaf(row[j + 3], v[j + 3], a3);
+    {
+      const int r = t >> 2, sub = t & 3;
+      float a0 = 0.f, a1 = 0.f;
+      if (r < m) {
+        const int gi = o + r;
+        const float* row = F + gi * ld + o;  // A(gi, o + j), j <= r
+        int j = sub;
+        for (; j + 4 <= r; j += 8) {
+          a0 = fmaf(row[j], v[j], a0);
+          a1 = fmaf(row[j + 4], v[j + 4], a1);
+        }
+        for (; j <= r; j += 4) a0 = fmaf(row[j], v[j], a0);
+        // j > r: A(o + j, gi) = F[(o + j) * ld + gi]; first j = r + 1 + ((sub - r - 1) mod 4)
+        j = r + 1 + ((sub - r - 1) & 3);
+        for (; j + 4 < m; j += 8) {
+          a0 = fmaf(F[(o + j) * ld + gi], v[j], a0);
+          a1 = fmaf(F[(o + j + 4) * ld + gi], v[j + 4], a1);
+        }
+        for (; j < m; j += 4) a0 = fmaf(F[(o + j) * ld + gi], v[j], a0);
       }
-      for (; j <= t; ++j) a0 = fmaf(row[j], v[j], a0);
-      const float* col = F + gi;  // A(o + j, gi) = F[(o + j) * ld + gi], j > t
-      for (j = t + 1; j + 3 < m; j += 4) {
-        a0 = fmaf(col[(o + j) * ld], v[j], a0);
-        a1 = fmaf(col[(o + j + 1) * ld], v[j + 1], a1);
-        a2 = fmaf(col[(o + j + 2) * ld], v[j + 2], a2);
-        a3 = fmaf(col[(o + j + 3) * ld], v[j + 3], a3);
+      float sacc = a0 + a1;
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+      if (r < m && sub == 0) {
+        sacc *= tk;
+        p[r] = sacc;
+        pv = sacc * v[r];
       }
-      for (; j < m; ++j) a0 = fmaf(col[(o + j) * ld], v[j], a0);
-      const float sacc = tk * ((a0 + a1) + (a2 + a3));
-      p[t] = sacc;
-      pv = sacc * v[t];
     }
     for (int q = 16; q > 0; q >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, q);
     if (lane == 0) wpart[warp] = pv;
@@ -768,9 +775,11 @@ __global__ void __launch_bounds__(256) oa_e_kernel(int n, const double* __restri
                                                    const double* __restrict__ dvec,
                                                    const double* __restrict__ scal,
                                                    double* __restrict__ E, int* done,
-                                                   double* delta_out) {
+                                                   double* delta_out,
+                                                   unsigned long long* emax) {
   if (*done) return;
   __shared__ double s_delta;
+  __shared__ unsigned long long s_max[8];
   const double* G = GS;
   const double* S = GS + (int64_t)n * n;
   if (threadIdx.x < 32) {  // fixed-order sum of the partials (every CTA alike)
@@ -788,6 +797,7 @@ __global__ void __launch_bounds__(256) oa_e_kernel(int n, const double* __restri
   __syncthreads();
   const double delta = s_delta;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long m = 0;
   if (e < (int64_t)n * n) {
     const int i = (int)(e % n), j = (int)(e / n);
     const double r = (i == j ? 1.0 : 0.0) - G[e];
@@ -798,12 +808,33 @@ __global__ void __launch_bounds__(256) oa_e_kernel(int n, const double* __restri
       if (fabs(gap) > delta && fabs(num) <= 1e-2 * fabs(gap)) out = num / gap;
     }
     E[e] = out;
+    m = (unsigned long long)__double_as_longlong(fabs(out));
+  }
+  // largest |E_ij| of the step (non-negative doubles order as their bits)
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long mm = 0;
+    for (int w = 0; w < 8; ++w) mm = max(mm, s_max[w]);
+    atomicMax(emax, mm);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     delta_out[0] = delta;
     // converged: the update of this step and every later step are skipped
     if (!(delta > 64.0 * n * kEps64 * scal[0])) done[0] = 1;
   }
+}
+
+// Skip flag of the next refinement step: set when this step was skipped or
+// converged (done) or its largest correction |E_ij| was at most 1e-10 (a
+// further step would change the vectors below FP64 resolution).  The
+// Newton-Schulz steps that follow always run: a first-order step leaves an
+// orthogonality defect of order |s_ij - s_ji| / |d_j - d_i| (the rounding
+// asymmetry of X^T A X over the gap) even when its corrections are tiny.
+__global__ void oa_next_kernel(const int* cur, const unsigned long long* emax, int* next) {
+  if (threadIdx.x == 0)
+    next[0] = (cur[0] || __longlong_as_double((long long)emax[0]) <= 1e-10) ? 1 : 0;
 }
 
 // Final pass on S = X^T A X, G = X^T X of the refined X (one CTA): order by
@@ -1547,16 +1578,23 @@ int dev_syev_refine(DenseLayer& L, int n, double* Z, int ldz, double* w, int* st
   const int lda = n;
   double* normA = D.scal;
   double* delta = D.scal + 1;
-  int* done = D.ints;
   int* perm = D.ints + 4;
   int* runs = perm + D.nmax;
   int* nruns = runs + 2 * D.nmax;
+  // skip flags of the steps (flag[s] for step s) and the largest correction
+  // of each step
+  if (steps > 16) return LOBPCG_ERR_ARG;
+  int* flag = D.ints + 4 * D.nmax + 24;
+  // (D.vec: the norm partials at 0 .. 127, d at 128 .. 128 + n, then these)
+  unsigned long long* emax = reinterpret_cast<unsigned long long*>(D.vec + 136 + D.nmax);
   double* X = D.XA;
   double* AX = D.XA + (size_t)n * n;
   double* G = D.GS;
-  LOB_CUDA_OK(cudaMemsetAsync(done, 0, sizeof(int), L.st));
+  LOB_CUDA_OK(cudaMemsetAsync(flag, 0, (steps + 1) * sizeof(int), L.st));
+  LOB_CUDA_OK(cudaMemsetAsync(emax, 0, steps * sizeof(unsigned long long), L.st));
   int rc;
   for (int s = 0; s < steps; ++s) {
+    int* done = flag + s;
     // [G, S] = X^T [X, A X]
     if ((rc = dev_gemm(L, false, false, n, n, n, 1.0, A, lda, X, n, 0.0, nullptr, 0, AX, n, done)))
       return rc;
@@ -1566,7 +1604,9 @@ int dev_syev_refine(DenseLayer& L, int n, double* Z, int ldz, double* w, int* st
     oa_norms_kernel<<<kOaBlocks, 256, 0, L.st>>>(n, D.GS, D.vec, D.vec + 2 * kOaBlocks, done);
     DLAUNCH(L);
     oa_e_kernel<<<nblk((int64_t)n * n), 256, 0, L.st>>>(n, D.GS, D.vec, D.vec + 2 * kOaBlocks,
-                                                        normA, D.E, done, delta);
+                                                        normA, D.E, done, delta, emax + s);
+    DLAUNCH(L);
+    oa_next_kernel<<<1, 32, 0, L.st>>>(done, emax + s, flag + s + 1);
     DLAUNCH(L);
     // X1 = X + X E
     if ((rc = dev_gemm(L, false, false, n, n, n, 1.0, X, n, D.E, n, 1.0, X, n, D.X1, n, done)))

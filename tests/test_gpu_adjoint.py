@@ -174,41 +174,45 @@ def test_adjoint_rejects_degenerate_pair():
 
 
 def test_adjoint_c5_full_size_properties():
-    """2D Laplacian 512 x 512 + diag(V) (n = 262,144), k = 32, tol 1e-8: the
-    gradient the oracle cannot form densely, checked by properties that hold
-    at any size: the eigenvalue-only gradient equals x_ri x_ci exactly;
-    Euler's identity <dL/dA, A> = sum_i lambda_i (the w_i terms vanish there
-    because every w_i is B-orthogonal to x_i).
-    The solve runs in FP64 with maxit 4000: this pencil's low, localised
-    states are nearly degenerate and the FP64 form needs ~2080 iterations."""
+    """2D Laplacian 512 x 512 + diag(V) (n = 262,144), loss over k = 32
+    pairs, tol 1e-8: the gradient the oracle cannot form densely, checked by
+    properties that hold at any size.  The complement operator's smallest
+    eigenvalue is lambda_33 - lambda_i, tiny for these localised, nearly
+    degenerate states, so the solve computes 40 pairs and the adjoint takes
+    all 40 with zero upstream gradients for pairs 33-40: pairs 33-40 enter
+    the explicit sum over computed pairs, the complement solve starts at
+    lambda_41 - lambda_i and its conjugate gradient converges (required).
+    Checks: the eigenvalue-only gradient equals x_ri x_ci exactly; Euler's
+    identity <dL/dA, A> = sum_i lambda_i (the w_i terms vanish there because
+    every w_i is B-orthogonal to x_i); the padded pairs contribute nothing."""
     torch = torch_cuda()
-    k = 32
+    k, kx = 32, 40
     p = synth.make_problem("lap2d_512_V", seed=0)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    s = gb.Solver(gemm_mode="f64", maxit=4000)
+    s = gb.Solver(gemm_mode="f64")
     s.set_operator(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val))
-    lam, X, it, be, rc = s.solve(k, 1e-8, device=True)
+    lam, X, it, be, rc = s.solve(kx, 1e-8, device=True)
     assert rc == gb.LOBPCG_OK
-    G = dev(synth.normal_block(0, synth.STREAM_GRAD, p.n, k))
-    glam = torch.ones(k, dtype=torch.float64, device="cuda")
-    # the complement operator's smallest eigenvalue is lambda_33 - lambda_32,
-    # tiny for these localised states, so the CG runs a bounded 2000
-    # iterations; its iterates stay B-orthogonal to X, which is all the
-    # identities below need
-    gA, _, its, rc = s.adjoint(k, lam, X, glam, G, cg_tol=CG_TOL, cg_maxit=2000,
+    G = torch.zeros(p.n, kx, dtype=torch.float64, device="cuda")
+    G[:, :k] = dev(synth.normal_block(0, synth.STREAM_GRAD, p.n, k))
+    glam = torch.zeros(kx, dtype=torch.float64, device="cuda")
+    glam[:k] = 1.0
+    # the pairs carry backward errors up to 1e-8, so the complement of X is
+    # invariant only to about 1e-8 / (lambda_41 - lambda_i): the conjugate
+    # gradient is asked for 1e-6 relative, above that floor
+    gA, _, its, rc = s.adjoint(kx, lam, X, glam, G, cg_tol=1e-6, cg_maxit=4000,
                                raise_on_error=False)
-    assert rc in (gb.LOBPCG_OK, gb.LOBPCG_ERR_NOT_CONVERGED) and its > 0
+    assert rc == gb.LOBPCG_OK and 0 < its < 4000, (rc, its)
     vals = dev(p.A.val)
     euler = float((gA * vals).sum())
     # for computed pairs the identity carries sum_i w_i^T r_i (r_i the
-    # residual, |r_i| ~ 1e-8 ||A||) and x_i^T w_i^in (X^T X = I to ~1e-12);
-    # measured 1.3e-7 relative: a wrong coefficient anywhere gives O(1)
-    assert abs(euler - float(lam.sum())) <= 1e-6 * float(lam.abs().sum()) + 1e-12 * float(
-        (gA.abs() * vals.abs()).sum())
-    gA1, _, its1, rc1 = s.adjoint(k, lam, X, glam, None)
+    # residual, |r_i| ~ 1e-8 ||A||) and x_i^T w_i^in (X^T X = I to ~1e-12)
+    lsum = float(lam[:k].sum())
+    assert abs(euler - lsum) <= 1e-6 * abs(lsum) + 1e-9 * float((gA.abs() * vals.abs()).sum())
+    gA1, _, its1, rc1 = s.adjoint(kx, lam, X, glam, None)
     assert rc1 == gb.LOBPCG_OK and its1 == 0
     rows = np.repeat(np.arange(p.n), np.diff(p.A.rowptr))
-    Xh = X.cpu().numpy()
+    Xh = X[:, :k].cpu().numpy()
     want = np.einsum("ei,ei->e", Xh[rows], Xh[p.A.col])
     assert np.abs(gA1.cpu().numpy() - want).max() <= 1e-14 * k
     s.close()
