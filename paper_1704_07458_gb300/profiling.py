@@ -265,7 +265,7 @@ def ksweep(workload, mode, ks, kw):
         p = synth.make_problem(workload, seed=0, k=k, **kw)
         nx = synth.block_width(p.k, p.n)
         X0 = torch.from_numpy(synth.normal_block(0, synth.STREAM_X0, p.n, nx)).cuda()
-        lam, st = _solve_once(p, dict(gemm_mode=mode, maxit=6000), X0, warm=False)
+        lam, st = _solve_once(p, dict(gemm_mode=mode, maxit=6000), X0, warm=True)
         out["points"].append({
             "k": k, "n_x": nx, "status": st["status"], "seconds": st["seconds"],
             "iterations": st["iterations"], "max_backward_error": st["max_backward_error"],
