@@ -78,10 +78,11 @@ def time_kernel(which, mode, slices, reps, warmup, n, s, m):
     if which == "update":
         S = torch.randn(n, s, generator=g, **dev)
         C = torch.randn(m * s, generator=g, **dev)
-        Y = torch.empty(n, m, **dev)
+        ldy = (m + 7) // 8 * 8  # the solver's blocks: leading dimension rounded up to 8 doubles
+        Y = torch.empty(n, ldy, **dev)
 
         def run():
-            rc = nat.lobpcg_update(n, S, s, s, C, s, m, 1.0, 0.0, None, 0, Y, m, mode_id,
+            rc = nat.lobpcg_update(n, S, s, s, C, s, m, 1.0, 0.0, None, 0, Y, ldy, mode_id,
                                    slices, st)
             assert rc == 0, rc
         flops = 2.0 * n * s * m

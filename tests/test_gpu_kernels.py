@@ -139,6 +139,33 @@ def test_update_parity(n, s, m, beta, mode, slices):
     assert np.all(np.abs(host(Yd, m) - ref) <= bound + 1e-300)
 
 
+@pytest.mark.parametrize("s,m", [(213, 142), (71, 40), (300, 96)])
+@pytest.mark.parametrize("slices", [6, 7])
+def test_update_parity_aligned_rows(s, m, slices):
+    """The tcgen05 update with the solver's padded layout: Y rows of
+    round_up(m, 8) doubles, so the epilogue's 32-byte stores run; checked
+    element by element against U C within the derived bound."""
+    torch = torch_cuda()
+    n = 3001
+    S = synth.normal_block(5, 1, n, s) * np.logspace(-8, 1, s)[None, :]
+    C = synth.normal_block(6, 1, s, m) * np.logspace(8, -1, s)[:, None]
+    ldy = (m + 7) // 8 * 8
+    Cd = dev(np.asfortranarray(C).T.copy().reshape(-1))
+    Yd = dev(np.zeros((n, m)), ldy)
+    assert Yd.data_ptr() % 32 == 0
+    rc = gb.lobpcg_update(n, dev(S, s), s, s, Cd, s, m, 1.0, 0.0, None, 0, Yd, ldy,
+                          gb.LOBPCG_GEMM_OZAKI_TC, slices)
+    torch.cuda.synchronize()
+    assert rc == 0
+    ref = ok.update(S, C)
+    Ct = np.abs(C) * (2 * np.abs(S).max(0))[:, None]
+    bound = (2 * gamma(s + 1) * (np.abs(S) @ np.abs(C)) + ozaki_unit(slices) * 4 * s *
+             Ct.max(0)[None, :] + 2.0 ** -52 * np.abs(ref))
+    got = host(Yd, m)
+    assert np.all(np.abs(got - ref) <= bound + 1e-300)
+    assert np.all(host(Yd)[:, m:] == 0)  # the padding columns are not written
+
+
 @pytest.mark.parametrize("n,m,c0", [(1, 1, 0), (300, 10, 0), (1024, 10, 4), (5000, 71, 70),
                                     (20000, 71, 3)])
 @pytest.mark.parametrize("bdiag", [False, True])
