@@ -30,7 +30,7 @@ def _spectrum_matrix(n, w, seed):
 def _cases():
     rng = np.random.default_rng(7)
     out = []
-    for n in (7, 18, 54, 213):
+    for n in (3, 7, 18, 54, 213, 224, 240):
         out.append(("separated", _spectrum_matrix(n, np.sort(rng.uniform(0, 10, n)), n)))
     w = np.sort(rng.uniform(0, 10, 71))
     w[10:13] = w[10] + np.array([0.0, 1e-9, 2e-12])
