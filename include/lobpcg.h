@@ -220,6 +220,27 @@ int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
                         const double* B_val, int64_t B_nnz, const double* B_diag,
                         int mem);
 
+/* Value types of lobpcg_set_operator_ex and its flags. */
+typedef enum { LOBPCG_F64 = 0, LOBPCG_F32 = 1 } lobpcg_dtype;
+enum { LOBPCG_BORROW = 1 };
+
+/* lobpcg_set_operator with the values of A, of a CSR B and of a diagonal B
+ * given as FP64 or FP32 (A_dtype, B_dtype, lobpcg_dtype).  FP32 values are
+ * widened to FP64 on entry (exactly); the solve computes in the form its
+ * options select, as after lobpcg_set_operator.  flags: LOBPCG_BORROW
+ * (device arrays only) makes the handle use the caller's CSR arrays in place
+ * instead of copying them (row pointers, columns, and FP64 values; FP32
+ * values are always widened into the handle's own copy, a diagonal B is
+ * always copied).  Borrowed arrays must stay allocated and unchanged until
+ * the handle is destroyed or given another operator; the handle never frees
+ * them.  Errors: as lobpcg_set_operator, and LOBPCG_ERR_ARG for a dtype
+ * other than LOBPCG_F64 / LOBPCG_F32, unknown flags, or LOBPCG_BORROW with
+ * host arrays. */
+int lobpcg_set_operator_ex(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
+                           const int32_t* A_col, const void* A_val, int64_t A_nnz, int A_dtype,
+                           const int32_t* B_rowptr, const int32_t* B_col, const void* B_val,
+                           int64_t B_nnz, const void* B_diag, int B_dtype, int mem, int flags);
+
 /* Diagonal preconditioner K = diag(kdiag) (n values, `mem` as above);
  * kdiag == NULL restores K = diag(A); a negative `mem` selects K = I.
  * Host values must be positive (LOBPCG_ERR_ARG otherwise). */

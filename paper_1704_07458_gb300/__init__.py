@@ -26,7 +26,7 @@ from ._native import (  # noqa: F401
     lobpcg_update, lobpcg_eig_adjoint, lobpcg_syev,
     lobpcg_residual, lobpcg_philox_normal, load, library_path,
     lobpcg_chebyshev_create, lobpcg_chebyshev_apply, lobpcg_chebyshev_destroy,
-    lobpcg_wait_selftest,
+    lobpcg_wait_selftest, lobpcg_set_operator_ex, LOBPCG_F64, LOBPCG_F32, LOBPCG_BORROW,
 )
 
 __all__ = [n for n in dir() if n.startswith("lobpcg_") or n.startswith("LOBPCG_")] + [
@@ -110,26 +110,39 @@ class Solver:
             return np.ascontiguousarray(x, dtype=dtype)
         if not (hasattr(x, "is_cuda") and x.is_cuda):
             raise ValueError(f"{name}: a host array among device arguments")
-        want = {np.int32: "torch.int32", np.float64: "torch.float64"}[dtype]
+        want = {np.int32: "torch.int32", np.float64: "torch.float64",
+                np.float32: "torch.float32"}[dtype]
         if str(x.dtype) != want:
             raise TypeError(f"{name}: device tensor must be {want}, got {x.dtype}")
         if not x.is_contiguous():
             raise ValueError(f"{name}: device tensor must be contiguous")
         return x
 
-    def set_operator(self, rowptr, col, val, b_diag=None, b_csr=None):
+    @staticmethod
+    def _f32(x):
+        """True for FP32 values (numpy float32 or a float32 tensor)."""
+        return x is not None and str(getattr(x, "dtype", "")) in ("float32", "torch.float32")
+
+    def set_operator(self, rowptr, col, val, b_diag=None, b_csr=None, borrow=False):
+        """Set the pencil (lobpcg_set_operator_ex).  FP32 values (numpy
+        float32 or float32 tensors) are passed as FP32 and widened by the
+        library; borrow=True (device tensors only) lets the handle use the CSR
+        tensors in place, which this object then keeps alive."""
         mem = self._mem(val)
         n = len(rowptr) - 1
         rowptr = self._arg(rowptr, mem, np.int32, "rowptr")
         col = self._arg(col, mem, np.int32, "col")
-        val = self._arg(val, mem, np.float64, "val")
+        a_dt = np.float32 if self._f32(val) else np.float64
+        val = self._arg(val, mem, a_dt, "val")
         if len(col) != len(val):
             raise ValueError("col and val differ in length")
-        args = dict(B_diag=self._arg(b_diag, mem, np.float64, "b_diag"))
+        b_src = b_csr[2] if b_csr is not None else b_diag
+        b_dt = np.float32 if self._f32(b_src) else np.float64
+        args = dict(B_diag=self._arg(b_diag, mem, b_dt, "b_diag"))
         if b_csr is not None:
             brp = self._arg(b_csr[0], mem, np.int32, "b_csr rowptr")
             bcol = self._arg(b_csr[1], mem, np.int32, "b_csr col")
-            bval = self._arg(b_csr[2], mem, np.float64, "b_csr val")
+            bval = self._arg(b_csr[2], mem, b_dt, "b_csr val")
             if len(brp) != n + 1 or len(bcol) != len(bval):
                 raise ValueError("b_csr does not match the size of A")
             args = dict(B_rowptr=brp, B_col=bcol, B_val=bval, B_nnz=len(bval))
@@ -137,7 +150,10 @@ class Solver:
             raise ValueError("b_diag must have n entries")
         self._keep = (rowptr, col, val, args)
         self.n = 0
-        rc = lobpcg_set_operator(self.h, n, rowptr, col, val, len(val), mem=mem, **args)
+        dt = lambda d: LOBPCG_F32 if d is np.float32 else LOBPCG_F64
+        rc = lobpcg_set_operator_ex(self.h, n, rowptr, col, val, len(val), dt(a_dt), mem=mem,
+                                    B_dtype=dt(b_dt), flags=LOBPCG_BORROW if borrow else 0,
+                                    **args)
         self._check(rc, "set_operator")
         self.n = n
 

@@ -20,6 +20,9 @@ LOBPCG_ERR_DEGENERATE = 8
 
 LOBPCG_MEM_HOST = 0
 LOBPCG_MEM_DEVICE = 1
+LOBPCG_F64 = 0
+LOBPCG_F32 = 1
+LOBPCG_BORROW = 1
 LOBPCG_GEMM_F64 = 0
 LOBPCG_GEMM_OZAKI = 1
 LOBPCG_GEMM_OZAKI_TC = 2
@@ -35,7 +38,7 @@ EXPORTED = [
     "lobpcg_update", "lobpcg_residual", "lobpcg_philox_normal", "lobpcg_gram_noalloc",
     "lobpcg_eig_adjoint", "lobpcg_syev",
     "lobpcg_chebyshev_create", "lobpcg_chebyshev_apply", "lobpcg_chebyshev_destroy",
-    "lobpcg_wait_selftest",
+    "lobpcg_wait_selftest", "lobpcg_set_operator_ex",
 ]
 
 
@@ -160,6 +163,8 @@ def load(build_if_missing=False):
         "lobpcg_chebyshev_apply": (I32, [P, I64, I64, P, I64, P, I64, P]),
         "lobpcg_chebyshev_destroy": (None, [P]),
         "lobpcg_wait_selftest": (I32, [I32, P]),
+        "lobpcg_set_operator_ex": (I32, [P, I64, P, P, P, I64, I32, P, P, P, I64, P, I32, I32,
+                                         I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +221,14 @@ def lobpcg_set_operator(h, n, A_rowptr, A_col, A_val, A_nnz, B_rowptr=None, B_co
     return lib.lobpcg_set_operator(h, n, ptr(A_rowptr), ptr(A_col), ptr(A_val), A_nnz,
                                    ptr(B_rowptr), ptr(B_col), ptr(B_val), B_nnz, ptr(B_diag),
                                    mem)
+
+
+def lobpcg_set_operator_ex(h, n, A_rowptr, A_col, A_val, A_nnz, A_dtype=LOBPCG_F64,
+                           B_rowptr=None, B_col=None, B_val=None, B_nnz=0, B_diag=None,
+                           B_dtype=LOBPCG_F64, mem=LOBPCG_MEM_HOST, flags=0):
+    return load().lobpcg_set_operator_ex(h, n, ptr(A_rowptr), ptr(A_col), ptr(A_val), A_nnz,
+                                         A_dtype, ptr(B_rowptr), ptr(B_col), ptr(B_val), B_nnz,
+                                         ptr(B_diag), B_dtype, mem, flags)
 
 
 def lobpcg_set_precond_diag(h, kdiag, mem=LOBPCG_MEM_HOST):

@@ -108,6 +108,9 @@ struct lobpcg_ctx {
   // operator
   int64_t n = 0, A_nnz = 0, B_nnz = 0;
   int32_t *A_rp = nullptr, *A_ci = nullptr, *B_rp = nullptr, *B_ci = nullptr;
+  // operator arrays used in place (lobpcg_set_operator_ex with LOBPCG_BORROW):
+  // bit 0 A_rp, 1 A_ci, 2 A_v, 3 B_rp, 4 B_ci, 5 B_v; never freed here
+  unsigned borrowed = 0;
   double *A_v = nullptr, *B_v = nullptr, *b_diag = nullptr;
   int b_kind = 0;  // 0 identity, 1 diagonal, 2 CSR
   double b_cond = 1.0;
@@ -145,11 +148,14 @@ struct lobpcg_ctx {
     ws_n = ws_nx = -1;
   }
   void release_op() {
+    int bit = 0;
     for (void** p : {(void**)&A_rp, (void**)&A_ci, (void**)&A_v, (void**)&B_rp, (void**)&B_ci,
                      (void**)&B_v, (void**)&b_diag, (void**)&adiag, (void**)&kdiag}) {
-      if (*p) cudaFree(*p);
+      if (*p && !((borrowed >> bit) & 1u)) cudaFree(*p);
       *p = nullptr;
+      ++bit;
     }
+    borrowed = 0;
   }
   void release_all() {
     free_ws();
@@ -1138,11 +1144,60 @@ LOBPCG_EXPORT int lobpcg_get_stats(lobpcg_t h, lobpcg_stats_t* out) {
   return LOBPCG_OK;
 }
 
-LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
-                                      const int32_t* A_col, const double* A_val, int64_t A_nnz,
-                                      const int32_t* B_rowptr, const int32_t* B_col,
-                                      const double* B_val, int64_t B_nnz, const double* B_diag,
-                                      int mem) {
+namespace {
+
+__global__ void widen_kernel(int64_t count, const float* __restrict__ src, double* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (double)src[i];
+}
+
+// value array of the operator into the handle: FP64 copied (or used in place
+// when borrowed), FP32 widened to FP64 (on the host for host arrays, by a
+// kernel for device arrays)
+int values_in(lobpcg_ctx* h, double** dst, const void* src, int64_t count, int dtype, int mem,
+              bool borrow, unsigned bit) {
+  if (dtype == LOBPCG_F64) {
+    if (borrow) {
+      *dst = static_cast<double*>(const_cast<void*>(src));
+      h->borrowed |= 1u << bit;
+      return LOBPCG_OK;
+    }
+    return copy_in(h, (void**)dst, src, (size_t)count * sizeof(double), mem);
+  }
+  if (mem == LOBPCG_MEM_HOST) {
+    const float* f = static_cast<const float*>(src);
+    std::vector<double> w(f, f + count);
+    return copy_in(h, (void**)dst, w.data(), (size_t)count * sizeof(double), LOBPCG_MEM_HOST);
+  }
+  if (cudaMalloc((void**)dst, std::max<size_t>((size_t)count * sizeof(double), 16)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return LOBPCG_ERR_OOM;
+  }
+  if (count > 0) {
+    widen_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, h->st>>>(
+        count, static_cast<const float*>(src), *dst);
+    ++g_launches;
+    if (cudaPeekAtLastError() != cudaSuccess) return LOBPCG_ERR_CUDA;
+  }
+  return LOBPCG_OK;
+}
+
+int index_in(lobpcg_ctx* h, int32_t** dst, const int32_t* src, int64_t count, int mem,
+             bool borrow, unsigned bit) {
+  if (borrow) {
+    *dst = const_cast<int32_t*>(src);
+    h->borrowed |= 1u << bit;
+    return LOBPCG_OK;
+  }
+  return copy_in(h, (void**)dst, src, (size_t)count * sizeof(int32_t), mem);
+}
+
+int set_operator_impl(lobpcg_t h, int64_t n, const int32_t* A_rowptr, const int32_t* A_col,
+                      const void* A_val, int64_t A_nnz, int A_dtype, const int32_t* B_rowptr,
+                      const int32_t* B_col, const void* B_val, int64_t B_nnz,
+                      const void* B_diag, int B_dtype, int mem, int flags) {
   if (!h) return LOBPCG_ERR_ARG;
   int dev = -1;
   cudaGetDevice(&dev);
@@ -1165,6 +1220,13 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
   if (B_rowptr && (!B_col || !B_val || B_nnz < 0 || B_nnz >= ((int64_t)1 << 31)))
     return drop(LOBPCG_ERR_ARG, "bad B");
   if (B_rowptr && B_diag) return drop(LOBPCG_ERR_ARG, "give B as CSR or diagonal, not both");
+  if ((A_dtype != LOBPCG_F64 && A_dtype != LOBPCG_F32) ||
+      (B_dtype != LOBPCG_F64 && B_dtype != LOBPCG_F32))
+    return drop(LOBPCG_ERR_ARG, "value dtype must be LOBPCG_F64 or LOBPCG_F32");
+  if ((flags & ~LOBPCG_BORROW) != 0) return drop(LOBPCG_ERR_ARG, "unknown flags");
+  const bool borrow = (flags & LOBPCG_BORROW) != 0;
+  if (borrow && mem != LOBPCG_MEM_DEVICE)
+    return drop(LOBPCG_ERR_ARG, "only device arrays can be borrowed");
   if (mem == LOBPCG_MEM_HOST) {
     // host arrays are checked before anything is copied: the kernels index
     // through rowptr and col without bounds checks
@@ -1180,8 +1242,11 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
     if (B_rowptr && !csr_ok(B_rowptr, B_col, B_nnz))
       return drop(LOBPCG_ERR_ARG, "B is not a valid n x n CSR");
     if (B_diag)
-      for (int64_t i = 0; i < n; ++i)
-        if (!(B_diag[i] > 0)) return drop(LOBPCG_ERR_ARG, "diagonal B must be positive");
+      for (int64_t i = 0; i < n; ++i) {
+        const double b = B_dtype == LOBPCG_F32 ? (double)static_cast<const float*>(B_diag)[i]
+                                               : static_cast<const double*>(B_diag)[i];
+        if (!(b > 0)) return drop(LOBPCG_ERR_ARG, "diagonal B must be positive");
+      }
   } else if (mem != LOBPCG_MEM_DEVICE) {
     return drop(LOBPCG_ERR_ARG, "mem must be LOBPCG_MEM_HOST or LOBPCG_MEM_DEVICE");
   }
@@ -1190,22 +1255,23 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
   h->n = n;
   h->A_nnz = A_nnz;
   int rc;
-  if ((rc = copy_in(h, (void**)&h->A_rp, A_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
-      (rc = copy_in(h, (void**)&h->A_ci, A_col, A_nnz * sizeof(int32_t), mem)) ||
-      (rc = copy_in(h, (void**)&h->A_v, A_val, A_nnz * sizeof(double), mem)))
+  if ((rc = index_in(h, &h->A_rp, A_rowptr, n + 1, mem, borrow, 0)) ||
+      (rc = index_in(h, &h->A_ci, A_col, A_nnz, mem, borrow, 1)) ||
+      (rc = values_in(h, &h->A_v, A_val, A_nnz, A_dtype, mem, borrow, 2)))
     return drop(rc, "copying A failed");
   h->b_kind = 0;
   h->b_cond = 1.0;
   if (B_rowptr) {
     h->b_kind = 2;
     h->B_nnz = B_nnz;
-    if ((rc = copy_in(h, (void**)&h->B_rp, B_rowptr, (n + 1) * sizeof(int32_t), mem)) ||
-        (rc = copy_in(h, (void**)&h->B_ci, B_col, B_nnz * sizeof(int32_t), mem)) ||
-        (rc = copy_in(h, (void**)&h->B_v, B_val, B_nnz * sizeof(double), mem)))
+    if ((rc = index_in(h, &h->B_rp, B_rowptr, n + 1, mem, borrow, 3)) ||
+        (rc = index_in(h, &h->B_ci, B_col, B_nnz, mem, borrow, 4)) ||
+        (rc = values_in(h, &h->B_v, B_val, B_nnz, B_dtype, mem, borrow, 5)))
       return drop(rc, "copying B failed");
   } else if (B_diag) {
     h->b_kind = 1;
-    if ((rc = copy_in(h, (void**)&h->b_diag, B_diag, n * sizeof(double), mem)))
+    // the diagonal is always copied into the handle (FP64), never borrowed
+    if ((rc = values_in(h, &h->b_diag, B_diag, n, B_dtype, mem, false, 6)))
       return drop(rc, "copying B failed");
     std::vector<double> b(n);
     if (cudaMemcpyAsync(b.data(), h->b_diag, n * sizeof(double), cudaMemcpyDeviceToHost, h->st) !=
@@ -1240,6 +1306,26 @@ LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_ro
       break;
     }
   return LOBPCG_OK;
+}
+
+}  // namespace
+
+LOBPCG_EXPORT int lobpcg_set_operator(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
+                                      const int32_t* A_col, const double* A_val, int64_t A_nnz,
+                                      const int32_t* B_rowptr, const int32_t* B_col,
+                                      const double* B_val, int64_t B_nnz, const double* B_diag,
+                                      int mem) {
+  return set_operator_impl(h, n, A_rowptr, A_col, A_val, A_nnz, LOBPCG_F64, B_rowptr, B_col,
+                           B_val, B_nnz, B_diag, LOBPCG_F64, mem, 0);
+}
+
+LOBPCG_EXPORT int lobpcg_set_operator_ex(lobpcg_t h, int64_t n, const int32_t* A_rowptr,
+                                         const int32_t* A_col, const void* A_val, int64_t A_nnz,
+                                         int A_dtype, const int32_t* B_rowptr,
+                                         const int32_t* B_col, const void* B_val, int64_t B_nnz,
+                                         const void* B_diag, int B_dtype, int mem, int flags) {
+  return set_operator_impl(h, n, A_rowptr, A_col, A_val, A_nnz, A_dtype, B_rowptr, B_col, B_val,
+                           B_nnz, B_diag, B_dtype, mem, flags);
 }
 
 LOBPCG_EXPORT int lobpcg_set_precond_diag(lobpcg_t h, const double* kdiag, int mem) {

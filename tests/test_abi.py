@@ -78,6 +78,8 @@ def test_host_side_argument_errors_without_gpu(lib):
     assert lib.lobpcg_get_stats(None, None) == gb.LOBPCG_ERR_ARG
     assert lib.lobpcg_last_error(None) == b"null handle"
     assert lib.lobpcg_wait_selftest(0, None) == gb.LOBPCG_ERR_ARG
+    assert lib.lobpcg_set_operator_ex(None, 4, None, None, None, 0, gb.LOBPCG_F32, None, None,
+                                      None, 0, None, gb.LOBPCG_F64, 0, 0) == gb.LOBPCG_ERR_ARG
 
 
 class _FakeDeviceTensor:

@@ -378,3 +378,44 @@ def test_c5_default_form_converges():
     assert st["slice_escalation_iteration"] == -1 or st["slice_escalation_iteration"] > 400
     _check_pairs(p, lam.cpu().numpy(), X.cpu().numpy(), be.cpu().numpy(), st["norm_a"],
                  st["norm_b"], tol_orth=1e-10)
+
+
+def test_operator_fp32_values_and_borrowed_device_csr():
+    """lobpcg_set_operator_ex: FP32 values of A and of a diagonal B (host and
+    device) are widened exactly, so the solve equals the FP64 call on the same
+    values; device CSR arrays used in place (LOBPCG_BORROW) give the same
+    solve and are neither modified nor freed by the handle; borrowing host
+    arrays and unknown dtypes are refused."""
+    torch = torch_cuda()
+    p = synth.make_problem("lap3d_64_diagB", N=16, k=16)
+    b32 = p.b_diag.astype(np.float32)
+    b64 = b32.astype(np.float64)
+    X0 = synth.normal_block(0, synth.STREAM_X0, p.n, synth.block_width(p.k, p.n))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def run(rowptr, col, val, bd, borrow=False):
+        with gb.Solver(gemm_mode="f64") as s:
+            s.set_operator(rowptr, col, val, b_diag=bd, borrow=borrow)
+            lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, raise_on_error=False)
+        assert rc == gb.LOBPCG_OK
+        return lam, it
+
+    lam64, it64 = run(p.A.rowptr, p.A.col, p.A.val, b64)
+    lam, it = run(p.A.rowptr, p.A.col, p.A.val.astype(np.float32), b32)
+    np.testing.assert_allclose(lam, lam64, rtol=1e-14)
+    assert it == it64
+    lam, it = run(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val.astype(np.float32)), dev(b32))
+    np.testing.assert_allclose(lam, lam64, rtol=1e-14)
+    rp, ci, va = dev(p.A.rowptr), dev(p.A.col), dev(p.A.val)
+    lam, it = run(rp, ci, va, dev(b64), borrow=True)
+    np.testing.assert_allclose(lam, lam64, rtol=1e-14)
+    torch.cuda.synchronize()
+    assert np.array_equal(va.cpu().numpy(), p.A.val) and np.array_equal(ci.cpu().numpy(), p.A.col)
+    lam, it = run(rp, ci, va, dev(b64), borrow=True)  # the same arrays again after close()
+    np.testing.assert_allclose(lam, lam64, rtol=1e-14)
+    with gb.Solver() as s:
+        rc = gb.lobpcg_set_operator_ex(s.h, p.n, p.A.rowptr, p.A.col, p.A.val, p.A.nnz,
+                                       gb.LOBPCG_F64, flags=gb.LOBPCG_BORROW)
+        assert rc == gb.LOBPCG_ERR_ARG
+        rc = gb.lobpcg_set_operator_ex(s.h, p.n, p.A.rowptr, p.A.col, p.A.val, p.A.nnz, 7)
+        assert rc == gb.LOBPCG_ERR_ARG
