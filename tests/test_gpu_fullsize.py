@@ -3,6 +3,10 @@
 tests/golden/oracle_lambda_<workload>.txt holds the eigenvalues the CPU
 oracle (plain FP64 Algorithm 8) reached on the full workload with the same
 seeded X0 and sketch Omega, written by tests/golden/make_oracle_lambda.py.
+The two largest workloads, beyond the oracle's reach, are pinned by their
+closed-form special cases at full size (the diffusion with sigma = 0, the
+Hamiltonian with a constant potential) and by a second solve from another
+start.
 The GPU solve of the same input must match them per eigenvalue: to relative
 1e-10 in the FP64 form and with 7-slice contractions, to 1e-9 with the
 default 6 slices (each emulated product is exact to 2^-44 relative to its
@@ -54,16 +58,18 @@ def _solve(p, **opts):
     return (lam.cpu().numpy(), X.cpu().numpy(), int(it), be.cpu().numpy(), rc, st)
 
 
-def _solve_dev(p, **opts):
-    """As _solve, outputs left on the device (torch tensors)."""
+def _solve_dev(p, seed=0, nx_extra=0, **opts):
+    """As _solve, outputs left on the device (torch tensors); seed picks the
+    X0 and sketch streams, nx_extra widens the block beyond the default."""
     torch = torch_cuda()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     s = gb.Solver(**opts)
     s.set_operator(dev(p.A.rowptr), dev(p.A.col), dev(p.A.val),
                    b_diag=None if p.b_diag is None else dev(p.b_diag))
-    nx = synth.block_width(p.k, p.n)
-    X0 = dev(synth.normal_block(0, synth.STREAM_X0, p.n, nx))
-    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, device=True, raise_on_error=False)
+    nx = min(synth.block_width(p.k, p.n) + nx_extra, p.n)
+    X0 = dev(synth.normal_block(seed, synth.STREAM_X0, p.n, nx))
+    lam, X, it, be, rc = s.solve(p.k, p.tol, X0=X0, seed=seed, device=True,
+                                 raise_on_error=False)
     st = s.stats()
     s.close()
     return lam, X, int(it), be, rc, st
@@ -152,8 +158,8 @@ def _properties_on_device(p, lam, X, st, tol_orth):
 def test_c3_full_size_properties():
     """128^3 log-normal diffusion (sigma = 1), B = I, Jacobi K, k = 256,
     tol 1e-8, default form: explicit Eq. (9), X^T X = I, and the spectrum of
-    the SPD operator positive.  No closed form: the oracle's eigenvalues are
-    compared at 16^3 in test_gpu_solve."""
+    the SPD operator positive.  The oracle's eigenvalues are compared at 16^3
+    in test_gpu_solve; the sigma = 0 closed form below pins the full size."""
     p = synth.make_problem("diffusion_128")
     lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
     assert rc == gb.LOBPCG_OK, rc
@@ -174,3 +180,156 @@ def test_c4_full_size_properties():
     assert float(lam[0]) >= 0 and float(lam[-1]) <= 16
     print(f"c4: {it} iterations, max backward error {bmax:.3e}, |X^T X - I| {orth:.2e}, "
           f"dropped columns {st['dropped_columns']}, switch at {st['flip_iteration']}")
+
+
+def _clusters(ref):
+    """Distinct values of a sorted closed-form spectrum (sums of 1-D
+    eigenvalues taken in different orders differ by a few ulps)."""
+    u = [ref[0]]
+    for v in ref[1:]:
+        if v - u[-1] > 1e-12 * max(1.0, abs(v)):
+            u.append(v)
+    return np.array(u)
+
+
+def _pairs_on_device(p, lam, X):
+    """For B = I, on the device with torch's own sparse product: the FP64
+    Rayleigh quotients rho_i = x_i^T A x_i / x_i^T x_i of the returned vectors,
+    ||A x_i - rho_i x_i|| / ||x_i|| and ||A x_i - lambda_i x_i|| / ||x_i||."""
+    torch = torch_cuda()
+    A = torch.sparse_csr_tensor(torch.from_numpy(p.A.rowptr.astype(np.int64)),
+                                torch.from_numpy(p.A.col.astype(np.int64)),
+                                torch.from_numpy(p.A.val), size=(p.n, p.n)).cuda()
+    AX = A @ X
+    xx = (X * X).sum(0)
+    rho = (X * AX).sum(0) / xx
+    rn_rho = torch.linalg.norm(AX - X * rho[None, :], dim=0) / xx.sqrt()
+    rn_lam = torch.linalg.norm(AX - X * lam[None, :], dim=0) / xx.sqrt()
+    return rho.cpu().numpy(), rn_rho.cpu().numpy(), rn_lam.cpu().numpy()
+
+
+def _closed_form_match(lam, rho, rn_rho, rn_lam, ref):
+    """Returned pairs against a closed-form spectrum with multiplicities.
+
+    Vectors: for a unit vector x with Rayleigh quotient rho and residual
+    r = A x - rho x, the eigenvalue mu nearest rho satisfies |rho - mu| <=
+    ||r||^2 / delta, delta the distance from rho to the rest of the spectrum
+    (the quadratic residual bound, Parlett 1980, Thm 11.7.1; it holds per
+    cluster of equal eigenvalues).  Values: the returned lambda_i comes from
+    the projected pencil, not from x_i, and ||A x - lambda x||^2 = ||r||^2 +
+    (lambda - rho)^2 ||x||^2, so |lambda_i - mu_i| <= ||A x_i - lambda_i x_i||
+    + |rho_i - mu_i|.  The matched mu, sorted, must equal the lowest k of the
+    closed form element by element, so a missed or doubled member of a
+    cluster fails even where every single pair is accurate.  Returns the
+    largest |lambda_i - mu_i| and |rho_i - mu_i|."""
+    u = _clusters(ref)
+    floor = 1e-13 * max(1.0, float(np.abs(ref).max()))
+    j = np.clip(np.searchsorted(u, rho), 1, len(u) - 1)
+    j = np.where(np.abs(u[j - 1] - rho) <= np.abs(u[j] - rho), j - 1, j)
+    mu = u[j]
+    lo = np.where(j > 0, rho - u[np.maximum(j - 1, 0)], np.inf)
+    hi = np.where(j < len(u) - 1, u[np.minimum(j + 1, len(u) - 1)] - rho, np.inf)
+    delta = np.minimum(lo, hi)
+    assert np.all(delta > rn_rho), "residuals too large for the quadratic bound"
+    err_rho = np.abs(rho - mu)
+    bound = rn_rho ** 2 / (delta - rn_rho) + floor
+    assert np.all(err_rho <= bound), (float((err_rho / bound).max()),
+                                      int(np.argmax(err_rho / bound)))
+    err_lam = np.abs(lam - mu)
+    assert np.all(err_lam <= rn_lam + bound), int(np.argmax(err_lam - rn_lam - bound))
+    k = len(lam)
+    ref_k = u[np.searchsorted(u, ref[:k] - 1e-12 * np.maximum(1.0, np.abs(ref[:k])))]
+    np.testing.assert_array_equal(np.sort(mu), ref_k)
+    return float(err_lam.max()), float(err_rho.max())
+
+
+def test_c3_sigma0_full_size_closed_form():
+    """c3 with sigma = 0: every face coefficient is exp(0) = 1, so the
+    operator is the 7-point Dirichlet Laplacian on 128^3, whose eigenvalues
+    are sums of three 1-D spectra 4 sin^2(pi j / (2 (N + 1))) (lambda_1 =
+    0.00177918092916, lambda_256 = 0.04380844413862).  Same k = 256, tol,
+    preconditioner and default form as the sigma = 1 workload."""
+    p = synth.make_problem("diffusion_128", sigma=0.0)
+    ref = synth.problems.closed_form_laplacian((128, 128, 128), p.k + 64)
+    np.testing.assert_allclose(ref[[0, 255]], [0.00177918092916, 0.04380844413862],
+                               rtol=1e-11)
+    lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
+    assert rc == gb.LOBPCG_OK, rc
+    bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
+    rho, rn_rho, rn_lam = _pairs_on_device(p, lam, X)
+    e_lam, e_rho = _closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
+    print(f"c3 sigma=0: {it} iterations, max backward error {bmax:.3e}, "
+          f"|X^T X - I| {orth:.2e}, max |lambda - closed form| {e_lam:.2e}, "
+          f"max |x^T A x - closed form| {e_rho:.2e}")
+
+
+# The solves below take 3 to 8 minutes each on one GB300; they run when
+# LOBPCG_LONG_TESTS=1.
+LONG = pytest.mark.skipif(os.environ.get("LOBPCG_LONG_TESTS") != "1",
+                          reason="long full-size solve; set LOBPCG_LONG_TESTS=1")
+
+
+def _periodic_closed_form(N, c, count):
+    """c + eigenvalues of -1/2 (periodic 7-point Laplacian) on N^3: sums of
+    three 1-D values 2 sin^2(pi j / N), j = 0 .. N-1."""
+    one = np.sort(2.0 * np.sin(np.pi * np.arange(N) / N) ** 2)
+    lam = np.zeros(1)
+    for _ in range(3):
+        lam = np.sort((lam[:, None] + one[None, :]).ravel())[: count * 4 + 64]
+    return c + lam[:count]
+
+
+@LONG
+def test_c4_constant_potential_full_size_closed_form():
+    """c4 with V = 5 everywhere (the mean of its U[0, 10] potential): H = -1/2
+    Laplacian on the periodic 96^3 torus + 5 I, same k = 1024, n_x = 1127,
+    tol and default form as the random-potential workload.  The closed
+    spectrum has clusters of up to 48 equal eigenvalues; the one at k spans
+    indices 1021-1044 and the one at n_x indices 1117-1140, so both block
+    edges cut through a cluster."""
+    N, c = 96, 5.0
+    A = synth.hamiltonian_3d_periodic(N, np.full(N ** 3, c))
+    p = synth.Problem("hamiltonian_96_V5", A, 1024, 1e-8, kdiag=A.diagonal())
+    ref = _periodic_closed_form(N, c, 1400)
+    lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
+    assert rc == gb.LOBPCG_OK, rc
+    bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
+    rho, rn_rho, rn_lam = _pairs_on_device(p, lam, X)
+    e_lam, e_rho = _closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
+    print(f"c4 V=5: {it} iterations, max backward error {bmax:.3e}, |X^T X - I| {orth:.2e}, "
+          f"max |lambda - closed form| {e_lam:.2e}, max |x^T A x - closed form| {e_rho:.2e}, "
+          f"dropped columns {st['dropped_columns']}")
+
+
+def _two_starts_agree(p):
+    """Two solves, the second from another seed's X0 and sketch with the
+    block 32 columns wider, must find the same k eigenvalues.  Each returned
+    lambda_i lies within ||A x_i - lambda_i x_i|| / ||x_i|| of an eigenvalue
+    (Weyl), so the runs differ by at most the sum of those residual norms."""
+    out = []
+    for seed, extra in ((0, 0), (1, 32)):
+        lam, X, it, be, rc, st = _solve_dev(p, seed=seed, nx_extra=extra, gemm_mode="ozaki_tc")
+        assert rc == gb.LOBPCG_OK, (seed, rc)
+        _properties_on_device(p, lam, X, st, 1e-10)
+        rn = _pairs_on_device(p, lam, X)[2]
+        out.append((lam.cpu().numpy(), rn, it))
+        del X
+    (l0, r0, i0), (l1, r1, i1) = out
+    d = np.abs(l0 - l1)
+    assert np.all(d <= r0 + r1 + 1e-13 * np.abs(l0).max()), (
+        float((d / (r0 + r1)).max()), int(np.argmax(d / (r0 + r1))))
+    return i0, i1, float((d / np.abs(l0)).max())
+
+
+@LONG
+def test_c3_two_starts_agree():
+    """c3 (sigma = 1) from seeds 0 and 1, n_x = 282 and 314."""
+    i0, i1, rel = _two_starts_agree(synth.make_problem("diffusion_128"))
+    print(f"c3 two starts: {i0} and {i1} iterations, max relative difference {rel:.2e}")
+
+
+@LONG
+def test_c4_two_starts_agree():
+    """c4 (V ~ U[0, 10]) from seeds 0 and 1, n_x = 1127 and 1159."""
+    i0, i1, rel = _two_starts_agree(synth.make_problem("hamiltonian_96"))
+    print(f"c4 two starts: {i0} and {i1} iterations, max relative difference {rel:.2e}")
