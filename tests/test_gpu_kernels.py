@@ -115,7 +115,8 @@ def test_gram_parity(n, p, q, mode, slices):
 
 
 @pytest.mark.parametrize("n,s,m", [(1, 4, 3), (65, 17, 9), (4099, 213, 142), (3000, 71, 71),
-                                   (1500, 530, 97), (700, 300, 96)])
+                                   (1500, 530, 97), (700, 300, 96), (2100, 213, 128),
+                                   (1300, 150, 113)])
 @pytest.mark.parametrize("beta", [0.0, 1.0])
 @pytest.mark.parametrize("mode,slices", MODES)
 def test_update_parity(n, s, m, beta, mode, slices):
