@@ -19,7 +19,8 @@
  *     it keeps.  Outputs go to caller-allocated buffers.
  *   - A handle may be used by one host thread at a time.
  *   - CSR matrices: int32 row pointers and column indices (nnz < 2^31), columns
- *     sorted within a row, float64 values; A and B must be symmetric.
+ *     sorted within a row, float64 values (float32 values are accepted by
+ *     lobpcg_set_operator_ex and widened on entry); A and B must be symmetric.
  */
 #ifndef GB300_LOBPCG_H
 #define GB300_LOBPCG_H
@@ -50,15 +51,17 @@ typedef enum { LOBPCG_MEM_HOST = 0, LOBPCG_MEM_DEVICE = 1 } lobpcg_mem;
 
 /* Arithmetic used for the n-scaled dense contractions (Gram S^T Y and basis
  * update S C).  F64 rounds like any FP64 dot product.  The emulated modes cut
- * each FP64 input of a 64-long chunk into `slices` exact BF16 digits against
- * the exponent bound of its chunk row or column; each term is then exact to
- * about 2^-44 (6 slices) or 2^-56 (7) relative to those bounds, and the sums
- * are accumulated in double-float.  Everything else (projected pencils,
- * Algorithm 7, norms, Eq. 9) runs in FP64 in every mode. */
+ * each FP64 input into `slices` exact BF16 digits against the exponent bound
+ * shared by its block of the contraction (64 long for mma.sync, 256 for
+ * tcgen05); each product is then exact to about 2^-44 (6 slices) or 2^-56 (7)
+ * relative to those bounds.  The mma.sync form sums the blocks in
+ * double-float, the tcgen05 form in int64 fixed point with one final
+ * rounding.  Everything else (projected pencils, Algorithm 7, norms, Eq. 9)
+ * runs in FP64 in every mode. */
 typedef enum {
   LOBPCG_GEMM_F64 = 0,      /* plain FP64 fused multiply-add on the CUDA cores */
   LOBPCG_GEMM_OZAKI = 1,    /* FP64 emulated by exact BF16 splits, warp-level mma.sync */
-  LOBPCG_GEMM_OZAKI_TC = 2  /* same splits; Grams on tcgen05 with TMEM accumulators */
+  LOBPCG_GEMM_OZAKI_TC = 2  /* same splits; Grams and updates on tcgen05, TMEM accumulators */
 } lobpcg_gemm_mode;
 
 /* Options; zero-initialise and set what you need, zeros select the defaults
