@@ -24,6 +24,7 @@ import synth
 import paper_1704_07458_gb300 as gb
 from oracle import lobpcg as L
 from gpu_util import torch_cuda
+from closed_form import closed_form_match, periodic_closed_form
 
 pytestmark = pytest.mark.gpu
 
@@ -182,16 +183,6 @@ def test_c4_full_size_properties():
           f"dropped columns {st['dropped_columns']}, switch at {st['flip_iteration']}")
 
 
-def _clusters(ref):
-    """Distinct values of a sorted closed-form spectrum (sums of 1-D
-    eigenvalues taken in different orders differ by a few ulps)."""
-    u = [ref[0]]
-    for v in ref[1:]:
-        if v - u[-1] > 1e-12 * max(1.0, abs(v)):
-            u.append(v)
-    return np.array(u)
-
-
 def _pairs_on_device(p, lam, X):
     """For B = I, on the device with torch's own sparse product: the FP64
     Rayleigh quotients rho_i = x_i^T A x_i / x_i^T x_i of the returned vectors,
@@ -208,41 +199,6 @@ def _pairs_on_device(p, lam, X):
     return rho.cpu().numpy(), rn_rho.cpu().numpy(), rn_lam.cpu().numpy()
 
 
-def _closed_form_match(lam, rho, rn_rho, rn_lam, ref):
-    """Returned pairs against a closed-form spectrum with multiplicities.
-
-    Vectors: for a unit vector x with Rayleigh quotient rho and residual
-    r = A x - rho x, the eigenvalue mu nearest rho satisfies |rho - mu| <=
-    ||r||^2 / delta, delta the distance from rho to the rest of the spectrum
-    (the quadratic residual bound, Parlett 1980, Thm 11.7.1; it holds per
-    cluster of equal eigenvalues).  Values: the returned lambda_i comes from
-    the projected pencil, not from x_i, and ||A x - lambda x||^2 = ||r||^2 +
-    (lambda - rho)^2 ||x||^2, so |lambda_i - mu_i| <= ||A x_i - lambda_i x_i||
-    + |rho_i - mu_i|.  The matched mu, sorted, must equal the lowest k of the
-    closed form element by element, so a missed or doubled member of a
-    cluster fails even where every single pair is accurate.  Returns the
-    largest |lambda_i - mu_i| and |rho_i - mu_i|."""
-    u = _clusters(ref)
-    floor = 1e-13 * max(1.0, float(np.abs(ref).max()))
-    j = np.clip(np.searchsorted(u, rho), 1, len(u) - 1)
-    j = np.where(np.abs(u[j - 1] - rho) <= np.abs(u[j] - rho), j - 1, j)
-    mu = u[j]
-    lo = np.where(j > 0, rho - u[np.maximum(j - 1, 0)], np.inf)
-    hi = np.where(j < len(u) - 1, u[np.minimum(j + 1, len(u) - 1)] - rho, np.inf)
-    delta = np.minimum(lo, hi)
-    assert np.all(delta > rn_rho), "residuals too large for the quadratic bound"
-    err_rho = np.abs(rho - mu)
-    bound = rn_rho ** 2 / (delta - rn_rho) + floor
-    assert np.all(err_rho <= bound), (float((err_rho / bound).max()),
-                                      int(np.argmax(err_rho / bound)))
-    err_lam = np.abs(lam - mu)
-    assert np.all(err_lam <= rn_lam + bound), int(np.argmax(err_lam - rn_lam - bound))
-    k = len(lam)
-    ref_k = u[np.searchsorted(u, ref[:k] - 1e-12 * np.maximum(1.0, np.abs(ref[:k])))]
-    np.testing.assert_array_equal(np.sort(mu), ref_k)
-    return float(err_lam.max()), float(err_rho.max())
-
-
 def test_c3_sigma0_full_size_closed_form():
     """c3 with sigma = 0: every face coefficient is exp(0) = 1, so the
     operator is the 7-point Dirichlet Laplacian on 128^3, whose eigenvalues
@@ -257,7 +213,7 @@ def test_c3_sigma0_full_size_closed_form():
     assert rc == gb.LOBPCG_OK, rc
     bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
     rho, rn_rho, rn_lam = _pairs_on_device(p, lam, X)
-    e_lam, e_rho = _closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
+    e_lam, e_rho = closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
     print(f"c3 sigma=0: {it} iterations, max backward error {bmax:.3e}, "
           f"|X^T X - I| {orth:.2e}, max |lambda - closed form| {e_lam:.2e}, "
           f"max |x^T A x - closed form| {e_rho:.2e}")
@@ -267,16 +223,6 @@ def test_c3_sigma0_full_size_closed_form():
 # LOBPCG_LONG_TESTS=1.
 LONG = pytest.mark.skipif(os.environ.get("LOBPCG_LONG_TESTS") != "1",
                           reason="long full-size solve; set LOBPCG_LONG_TESTS=1")
-
-
-def _periodic_closed_form(N, c, count):
-    """c + eigenvalues of -1/2 (periodic 7-point Laplacian) on N^3: sums of
-    three 1-D values 2 sin^2(pi j / N), j = 0 .. N-1."""
-    one = np.sort(2.0 * np.sin(np.pi * np.arange(N) / N) ** 2)
-    lam = np.zeros(1)
-    for _ in range(3):
-        lam = np.sort((lam[:, None] + one[None, :]).ravel())[: count * 4 + 64]
-    return c + lam[:count]
 
 
 @LONG
@@ -290,12 +236,12 @@ def test_c4_constant_potential_full_size_closed_form():
     N, c = 96, 5.0
     A = synth.hamiltonian_3d_periodic(N, np.full(N ** 3, c))
     p = synth.Problem("hamiltonian_96_V5", A, 1024, 1e-8, kdiag=A.diagonal())
-    ref = _periodic_closed_form(N, c, 1400)
+    ref = periodic_closed_form(N, c, 1400)
     lam, X, it, be, rc, st = _solve_dev(p, gemm_mode="ozaki_tc")
     assert rc == gb.LOBPCG_OK, rc
     bmax, orth = _properties_on_device(p, lam, X, st, 1e-10)
     rho, rn_rho, rn_lam = _pairs_on_device(p, lam, X)
-    e_lam, e_rho = _closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
+    e_lam, e_rho = closed_form_match(lam.cpu().numpy(), rho, rn_rho, rn_lam, ref)
     print(f"c4 V=5: {it} iterations, max backward error {bmax:.3e}, |X^T X - I| {orth:.2e}, "
           f"max |lambda - closed form| {e_lam:.2e}, max |x^T A x - closed form| {e_rho:.2e}, "
           f"dropped columns {st['dropped_columns']}")
