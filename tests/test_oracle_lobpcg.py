@@ -515,3 +515,77 @@ def test_zero_b_norm_column_reading():
     assert W.shape[1] == 4
     np.testing.assert_allclose(W.T @ Bm(W), np.eye(4), atol=1e-12)
     np.testing.assert_allclose(V.T @ Bm(W), 0, atol=1e-12)
+
+
+def _random_sparse_symmetric(n, seed, per_row=4, stream=synth.STREAM_COEF):
+    """A random sparse symmetric CSR matrix from the seeded generator: about
+    per_row off-diagonal pairs per row with N(0, 1) values and a N(0, 1)
+    diagonal (so the spectrum is indefinite)."""
+    import scipy.sparse as sp
+    m = n * per_row
+    u = synth.uniform_block(seed, stream, 2 * m)
+    i = np.minimum((u[:m] * n).astype(np.int64), n - 1)
+    j = np.minimum((u[m:] * n).astype(np.int64), n - 1)
+    v = synth.normal_flat(seed, stream, 2 * m, m)
+    d = synth.normal_flat(seed, stream, 3 * m, n)
+    S = sp.coo_matrix((v, (i, j)), shape=(n, n)).tocsr()
+    S = S + S.T + sp.diags(d)
+    S = sp.csr_matrix(S)
+    S.sort_indices()
+    return S
+
+
+def _csr(S):
+    return synth.CSR(S.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32),
+                     S.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("n,k,bkind,seed", [(40, 3, "identity", 11), (90, 6, "diag", 12),
+                                            (160, 4, "csr", 13), (200, 8, "diag", 14),
+                                            (120, 1, "csr", 15)])
+def test_brute_force_random_pencils(n, k, bkind, seed):
+    """Algorithm 8 on random sparse symmetric A (indefinite) with B = I, a
+    diagonal B ~ U[1, 2] or a sparse SPD B = I + 0.1 (S + S^T) / ||S + S^T||_inf,
+    against a dense generalised eigensolver (LAPACK through scipy, independent
+    of the oracle): lambda within the first-order bound of Eq. (9)'s residual,
+    X^T B X = I, and Eq. (9) recomputed on the returned pairs."""
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    S = _random_sparse_symmetric(n, seed)
+    A = _csr(S)
+    Ad = S.toarray()
+    if bkind == "identity":
+        b, Bd = None, np.eye(n)
+    elif bkind == "diag":
+        b = synth.uniform_block(seed, synth.STREAM_BDIAG, n, 1.0, 2.0)
+        Bd = np.diag(b)
+    else:
+        T = _random_sparse_symmetric(n, seed + 100, per_row=2, stream=synth.STREAM_POTENTIAL)
+        T = T - sp.diags(T.diagonal())
+        T = T * (0.1 / abs(T).sum(axis=1).max())
+        Bm = sp.csr_matrix(sp.identity(n) + T)
+        Bm.sort_indices()
+        b = (Bm.indptr.astype(np.int32), Bm.indices.astype(np.int32), Bm.data)
+        Bd = Bm.toarray()
+    kdiag = np.abs(Ad.diagonal()) + 1.0
+    pen = L.Pencil(n, (A.rowptr, A.col, A.val), b, kdiag)
+    nx = synth.block_width(k, n)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, n, 16).T
+    tol = 1e-10
+    r = L.lobpcg(pen, X0, k, tol, Om)
+    assert r.status == L.OK, r.status
+    w = sla.eigh(Ad, Bd, eigvals_only=True, subset_by_index=[0, k - 1])
+    X = r.X[:, :k]
+    BX = Bd @ X
+    np.testing.assert_allclose(X.T @ BX, np.eye(k), atol=1e-12)
+    R = Ad @ X - BX * r.lam[None, :]
+    # Eq. (9) on the returned pairs with the solve's own norm estimates
+    be = np.linalg.norm(R, axis=0) / (
+        (r.normA + np.abs(r.lam) * r.normB) * np.linalg.norm(X, axis=0))
+    assert np.all(be <= tol * (1 + 1e-6)), be.max()
+    # a pair with B-residual r has an eigenvalue within ||r||_{B^-1} / ||x||_B;
+    # here ||x||_B = 1 and ||r||_{B^-1} <= ||r|| / sqrt(lambda_min(B))
+    lmin_b = np.linalg.eigvalsh(Bd)[0]
+    bound = np.linalg.norm(R, axis=0) / np.sqrt(lmin_b) + 1e-13 * np.abs(w).max()
+    assert np.all(np.abs(r.lam - w) <= bound), (np.abs(r.lam - w) / bound).max()
