@@ -28,6 +28,7 @@ import argparse
 import collections
 import csv
 import json
+import os
 import sys
 
 SCALE = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
@@ -278,6 +279,19 @@ def ksweep(workload, mode, ks, kw):
     return out
 
 
+def mma_rate():
+    """Build and run the standalone tcgen05.mma rate probe
+    (csrc/probes/tcgen05_mma_rate.cu): cycles per M = 128, K = 16 MMA against
+    N, operand layout and issuing thread.  Needs a GB300; prints its lines."""
+    import subprocess
+    from . import build as b
+    src = os.path.join(os.path.dirname(__file__), "csrc", "probes", "tcgen05_mma_rate.cu")
+    exe = os.path.join(b.OUT, "tcgen05_mma_rate")
+    os.makedirs(b.OUT, exist_ok=True)
+    subprocess.run([b._nvcc(), *b.ARCH, "-O3", "-o", exe, src], check=True)
+    return subprocess.run([exe], check=True).returncode
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -304,7 +318,10 @@ def main(argv=None):
     ks.add_argument("--mode", default="ozaki_tc", choices=["f64", "ozaki", "ozaki_tc"])
     ks.add_argument("--ks", default="16,32,64,128")
     ks.add_argument("--N", type=int, default=0)
+    sub.add_parser("mma-rate")
     a = ap.parse_args(argv)
+    if a.cmd == "mma-rate":
+        return mma_rate()
     if a.cmd == "versions":
         kw = {kk: vv for kk, vv in (("N", a.N), ("k", a.k)) if vv}
         return versions(a.workload, a.mode, kw)
