@@ -1,6 +1,6 @@
 """Host-side tooling of the benchmark and the profiles, on CPU: the ncu
 launch-list summary, the clock sampler's parsing and the digit-pair count of
-the emulated contractions."""
+the emulated contractions, and that the tcgen05.mma rate probe builds."""
 import io
 import os
 import sys
@@ -65,3 +65,19 @@ def test_clock_sampler_parses_reasons(tmp_path):
     r = c.stop()
     assert r["sm_mhz"] == 2070 and r["sm_max_mhz"] == 2070 and r["samples"] == 3
     assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_mma_rate_probe_compiles(tmp_path):
+    """The standalone tcgen05.mma rate probe behind `profiling mma-rate`
+    builds for sm_103a (it runs only on a GB300)."""
+    import shutil
+    import subprocess
+    from paper_1704_07458_gb300 import build as b
+    try:
+        nvcc = b._nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not found")
+    src = os.path.join(os.path.dirname(b.__file__), "csrc", "probes", "tcgen05_mma_rate.cu")
+    out = str(tmp_path / "tcgen05_mma_rate")
+    subprocess.run([nvcc, *b.ARCH, "-O3", "-o", out, src], check=True)
+    assert os.path.exists(out)
