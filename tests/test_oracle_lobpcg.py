@@ -589,3 +589,33 @@ def test_brute_force_random_pencils(n, k, bkind, seed):
     lmin_b = np.linalg.eigvalsh(Bd)[0]
     bound = np.linalg.norm(R, axis=0) / np.sqrt(lmin_b) + 1e-13 * np.abs(w).max()
     assert np.all(np.abs(r.lam - w) <= bound), (np.abs(r.lam - w) / bound).max()
+
+
+class _Fp32Products(L.Pencil):
+    """The pencil with every product A X rounded as an FP32 sparse product
+    (values and block in FP32): a model of an FP32-storage form."""
+
+    def A_mul(self, X):
+        return np.asarray(self.A.astype(np.float32) @ X.astype(np.float32), dtype=np.float64)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp32_a_products_level_off_above_tol_1e8(seed):
+    """With A X rounded to FP32 the residual of Eq. (9) carries errors of
+    order 2^-24 ||A|| ||x||: Algorithm 8 on c1 still reaches backward error
+    1e-6 in about the FP64 iteration count, but not 1e-8 within 400
+    iterations (the FP64 oracle needs about 100).  Why a form with FP32 A
+    products needs an FP64-product phase to report tol 1e-8."""
+    p = synth.make_problem("lap2d_32")
+    A = p.A
+    nx = synth.block_width(p.k, A.n)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, A.n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, A.n, 16).T
+    pen64 = L.Pencil(A.n, (A.rowptr, A.col, A.val), None, A.diagonal())
+    r64 = L.lobpcg(pen64, X0, p.k, 1e-8, Om)
+    assert r64.status == L.OK and r64.iters < 200
+    pen32 = _Fp32Products(A.n, (A.rowptr, A.col, A.val), None, A.diagonal())
+    r = L.lobpcg(pen32, X0, p.k, 1e-6, Om, L.Options(maxit=400))
+    assert r.status == L.OK and r.iters < 200
+    r = L.lobpcg(pen32, X0, p.k, 1e-8, Om, L.Options(maxit=400))
+    assert r.status == L.NOT_CONVERGED
