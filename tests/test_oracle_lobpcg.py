@@ -619,3 +619,30 @@ def test_fp32_a_products_level_off_above_tol_1e8(seed):
     assert r.status == L.OK and r.iters < 200
     r = L.lobpcg(pen32, X0, p.k, 1e-8, Om, L.Options(maxit=400))
     assert r.status == L.NOT_CONVERGED
+
+
+@pytest.mark.parametrize("name,kw,seed", [("lap2d_32", {}, 0), ("lap2d_32", {}, 1),
+                                          ("lap3d_64_diagB", {"N": 16, "k": 16}, 1)])
+def test_two_phase_fp32_then_fp64_schedule(name, kw, seed):
+    """A model of a two-phase precision schedule: Algorithm 8 with FP32
+    A-products to backward error 1e-5, then the FP64 solve restarted from
+    its k vectors (padded with the start block's other columns) to 1e-8.  The two phases together take about the FP64 solve's
+    iterations (within 15 %), most of them in the FP32 phase, and reach the
+    same eigenvalues."""
+    p = synth.make_problem(name, **kw)
+    A = p.A
+    nx = synth.block_width(p.k, A.n)
+    X0 = synth.normal_block(seed, synth.STREAM_X0, A.n, nx)
+    Om = synth.normal_block(seed, synth.STREAM_OMEGA, A.n, 16).T
+    pen64 = L.Pencil(A.n, (A.rowptr, A.col, A.val), p.b_diag, A.diagonal())
+    pen32 = _Fp32Products(A.n, (A.rowptr, A.col, A.val), p.b_diag, A.diagonal())
+    r64 = L.lobpcg(pen64, X0, p.k, 1e-8, Om)
+    r1 = L.lobpcg(pen32, X0, p.k, 1e-5, Om, L.Options(maxit=400))
+    assert r64.status == L.OK and r1.status == L.OK
+    # phase 2 starts from the k returned vectors and the remaining start columns
+    X1 = np.hstack([r1.X[:, :p.k], X0[:, p.k:]])
+    r2 = L.lobpcg(pen64, X1, p.k, 1e-8, Om)
+    assert r2.status == L.OK
+    assert r1.iters + r2.iters <= 1.15 * r64.iters
+    assert r1.iters >= r2.iters
+    np.testing.assert_allclose(r2.lam, r64.lam, rtol=1e-11)
